@@ -1,0 +1,296 @@
+"""Benchmark of the 2DSW time step (4096 x 4096 wet/dry workload, FP32).
+
+One benchmark step = 100 model time steps of the 4096^2 grid (the fused
+momentum / continuity / Shapiro / update kernel, temporally blocked) plus
+the FP64 volume reduction, i.e. every 2DSW row of the hot path.  The state
+(268 MB of eta, u, v, H) is larger than the 129 MB L2, so no L2 flush is
+needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gbsw|reference]
+
+Prints one JSON line.  Under torchrun (N > 1) every rank runs an
+independent replica (the workload has no exchange step), the timed region
+is bracketed by barriers and the slowest rank's time is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_CELLS_SIDE = 4096
+STEPS_PER_BENCH_STEP = 100
+BYTES_PER_CELL_UPDATE = 28  # read eta, u, v, H; write eta, u, v (FP32)
+METRIC = "cell-updates/s"
+WORKLOAD = "2DSW 4096x4096 wet/dry (15% dry), FP32, 100 time steps + FP64 volume per step"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampler run during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(n_gpus):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if _cuda_ok() else "gloo")
+    return rank, world, local
+
+
+def _cuda_ok():
+    import torch
+    return torch.cuda.is_available()
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if _cuda_ok() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_oracle_rate(nsteps=10, side=N_CELLS_SIDE):
+    """Time the FP64 oracle (single thread) on a bounded sample: nsteps time
+    steps of the full 4096^2 grid (the same synthetic input)."""
+    import oracle
+    from paper_1711_04471_gb300 import inputs
+    inp = inputs.sw_wetdry(n=side, seed=1001)
+    s = oracle.SWState(inp.params(), inp.H, inp.eta0)
+    t0 = time.perf_counter()
+    s.run(nsteps)
+    dt = time.perf_counter() - t0
+    return side * side * nsteps / dt, dt
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the FP64 CPU oracle, as it stands, on the host cores."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_1711_04471_gb300 import inputs
+    inp = inputs.sw_wetdry(n=N_CELLS_SIDE, seed=1001)
+    s = oracle.SWState(inp.params(), inp.H, inp.eta0)
+    for _ in range(args.warmup):
+        s.run(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s.run(1)
+    dt = time.perf_counter() - t0
+    cells = N_CELLS_SIDE ** 2 * args.steps
+    value = cells / dt
+    sample = f"{args.steps} time steps of the full 4096^2 grid (1 model step per bench step), FP64, 1 thread"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "grid": [N_CELLS_SIDE, N_CELLS_SIDE]},
+        "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_gbsw(args, rank, world, local):
+    import numpy as np
+    import torch
+
+    import paper_1711_04471_gb300 as P
+    from paper_1711_04471_gb300 import inputs
+    from paper_1711_04471_gb300.sw import SW
+
+    P.build()
+    torch.cuda.set_device(local)
+    dev_index = torch.cuda.current_device()
+    stream = torch.cuda.current_stream()
+    inp = inputs.sw_wetdry(n=N_CELLS_SIDE, seed=1001)
+    cells = N_CELLS_SIDE * N_CELLS_SIDE
+    sw = SW(inp.params(), inp.H, inp.eta0, stream=stream)
+    if args.blocking:
+        sw.set_blocking(args.blocking)
+    T = args.blocking or 4
+    launches_per_step = math.ceil(STEPS_PER_BENCH_STEP / T) + 2
+
+    # ---- device-resident throughput (value) ----
+    for _ in range(args.warmup):
+        sw.step(STEPS_PER_BENCH_STEP)
+        sw.volume()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    vols = []
+    clocks = ClockSampler(dev_index)
+    clocks.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        sw.step(STEPS_PER_BENCH_STEP)
+        ev[k][1].record(stream)
+        vols.append(sw.volume())  # synchronises: the step's result is read back
+    end.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    t_ms = start.elapsed_time(end)
+    t_ms = max_over_ranks(t_ms, world)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    fused_launch_ms = sum(step_ms) / (args.steps * math.ceil(STEPS_PER_BENCH_STEP / T))
+    value = cells * STEPS_PER_BENCH_STEP * args.steps * world / (t_ms * 1e-3)
+
+    # ---- end to end through the public API with host buffers ----
+    ny = nx = N_CELLS_SIDE
+    eta_h = torch.empty((ny, nx), dtype=torch.float32).pin_memory().numpy()
+    u_h = torch.empty((ny, nx + 1), dtype=torch.float32).pin_memory().numpy()
+    v_h = torch.empty((ny + 1, nx), dtype=torch.float32).pin_memory().numpy()
+    sw.get_state(eta=eta_h, u=u_h, v=v_h, want=("eta", "u", "v"))
+    e2e_steps = max(3, args.steps // 3)
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        sw.set_state(eta_h, u_h, v_h)
+        sw.step(STEPS_PER_BENCH_STEP)
+        sw.volume()
+        sw.get_state(eta=eta_h, u=u_h, v=v_h, want=("eta", "u", "v"))
+    t_e2e = max_over_ranks(time.perf_counter() - t0, world)
+    h2d = eta_h.nbytes + u_h.nbytes + v_h.nbytes
+    d2h = h2d + 3 * 8
+    e2e_value = cells * STEPS_PER_BENCH_STEP * e2e_steps * world / t_e2e
+    sw.close()
+
+    if rank != 0:
+        return
+    peak, peak_kind = _peaks()
+    achieved_gbs = BYTES_PER_CELL_UPDATE * cells * T / (fused_launch_ms * 1e-3) / 1e9
+    compulsory_gbs = BYTES_PER_CELL_UPDATE * cells / (fused_launch_ms * 1e-3) / 1e9
+    cpu_value, cpu_s = (None, None)
+    if world == 1 and not args.no_cpu_baseline:
+        cpu_value, cpu_s = cpu_oracle_rate()
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": [nx, ny], "time_steps_per_step": STEPS_PER_BENCH_STEP,
+                   "steps_per_launch": T, "l2": "state 268 MB > 129 MB L2, no flush needed",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": peak, "unit": "GB/s",
+                     "frac": achieved_gbs / peak, "traffic": args.traffic,
+                     "peak_kind": peak_kind, "kernel": "sw_fused_kernel",
+                     "per_unit": f"{BYTES_PER_CELL_UPDATE} B/cell-update x {T} steps x {cells} cells per launch",
+                     "compulsory_gbs": compulsory_gbs, "compulsory_frac": compulsory_gbs / peak,
+                     "launch_ms": fused_launch_ms},
+        "cpu_baseline": None if cpu_value is None else {
+            "value": cpu_value, "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": f"10 time steps of the full 4096^2 grid, FP64 oracle, 1 thread ({cpu_s:.1f} s)"},
+        "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk,
+        "volume_drift": (vols[-1][0] - vols[0][0]) / vols[0][0],
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gbsw", choices=["gbsw", "reference"])
+    ap.add_argument("--blocking", type=int, default=0)
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="ncu DRAM bytes per fused launch, if captured for this kernel version")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank, world, local = dist_setup(args.gpus)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_gbsw(args, rank, world, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,99 @@
+// Shared host/device helpers of the gbsw CUDA library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include "../../include/gbsw.h"
+
+namespace gbsw {
+
+// Device status word values (first writer wins, see set_device_status).
+enum : int { DEV_OK = 0, DEV_BOUNDS = 1, DEV_TIMEOUT = 2, DEV_NONFINITE = 3 };
+
+__device__ __forceinline__ void set_device_status(int *status, int code)
+{
+    atomicCAS(status, DEV_OK, code);
+}
+
+inline gbsw_status dev_status_to_gbsw(int s)
+{
+    switch (s) {
+    case DEV_OK: return GBSW_OK;
+    case DEV_BOUNDS: return GBSW_ERR_DEVICE_BOUNDS;
+    case DEV_TIMEOUT: return GBSW_ERR_TIMEOUT;
+    case DEV_NONFINITE: return GBSW_ERR_NONFINITE;
+    default: return GBSW_ERR_CUDA;
+    }
+}
+
+// Remember the last CUDA error text for diagnostics.
+void record_cuda_error(cudaError_t e, const char *what, const char *file, int line);
+
+#define GBSW_CUDA_TRY(expr)                                                   \
+    do {                                                                      \
+        cudaError_t _e = (expr);                                              \
+        if (_e != cudaSuccess) {                                              \
+            ::gbsw::record_cuda_error(_e, #expr, __FILE__, __LINE__);         \
+            return _e == cudaErrorMemoryAllocation ? GBSW_ERR_OOM : GBSW_ERR_CUDA; \
+        }                                                                     \
+    } while (0)
+
+#define GBSW_LAUNCH_CHECK()                                                   \
+    do {                                                                      \
+        cudaError_t _e = cudaGetLastError();                                  \
+        if (_e != cudaSuccess) {                                              \
+            ::gbsw::record_cuda_error(_e, "kernel launch", __FILE__, __LINE__); \
+            return GBSW_ERR_CUDA;                                             \
+        }                                                                     \
+    } while (0)
+
+inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+inline size_t round_up(size_t a, size_t b) { return (a + b - 1) / b * b; }
+
+// Number of SMs of the current device (cached per process).
+int sm_count();
+
+// ---------------------------------------------------------------------------
+// Deterministic FP64 block reduction: every thread contributes one value;
+// the warp tree (shuffle down by 16, 8, 4, 2, 1) and then a fixed-order
+// tree over warps give a result that depends only on the launch shape.
+// ---------------------------------------------------------------------------
+template <int NWARPS>
+__device__ __forceinline__ double block_sum_f64(double v, double *smem)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) smem[warp] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (warp == 0) {
+        r = lane < NWARPS ? smem[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+    }
+    __syncthreads();
+    return r;  // valid in thread 0
+}
+
+template <int NWARPS>
+__device__ __forceinline__ double block_min_f64(double v, double *smem)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_down_sync(0xffffffffu, v, o));
+    if (lane == 0) smem[warp] = v;
+    __syncthreads();
+    double r = INFINITY;
+    if (warp == 0) {
+        r = lane < NWARPS ? smem[lane] : INFINITY;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) r = fmin(r, __shfl_down_sync(0xffffffffu, r, o));
+    }
+    __syncthreads();
+    return r;
+}
+
+}  // namespace gbsw

@@ -1,0 +1,265 @@
+// 2-D shallow-water time step (Sec. 6.2 of arXiv:1711.04471: the predictor
+// "dyn", the first-order Shapiro filter "shapiro" and the state update),
+// as one fused, temporally blocked CUDA kernel, plus the FP64 volume
+// reduction.  The three map kernels the paper's compiler generates for this
+// loop are fused here into one pass over a shared-memory tile: each launch
+// loads eta, H, u, v once for a TX x TY tile plus a halo of 2*T cells, runs
+// T time steps in shared memory (the valid region shrinks by 2 cells per
+// step, the radius of one step's dependency cone) and writes the tile back.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+#include "sw_kernels.cuh"
+
+using namespace gbsw;
+
+struct gbsw_sw {
+    gbsw_sw_params p;
+    SWDev d;
+    cudaStream_t stream;
+    float *H;
+    float *eta[2], *u[2], *v[2];
+    int cur;
+    int blocking;           // 0 = automatic
+    double *partials;       // SW_VOL_BLOCKS * 3 doubles (scratch of the volume reduction)
+    double *result;         // 3 doubles on the device
+    double *h_result;       // 3 doubles, pinned host
+    uint8_t *wet;           // ny*nx bytes, staging for sw_get_state
+};
+
+namespace {
+
+template <int T, int TX, int TY>
+cudaError_t launch_fused(const gbsw_sw *s, const float *eta_in, const float *u_in, const float *v_in,
+                         float *eta_out, float *u_out, float *v_out)
+{
+    constexpr size_t smem = SWTile<T, TX, TY>::smem_bytes;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(sw_fused_kernel<T, TX, TY>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    dim3 grid(ceil_div(s->d.nx, TX), ceil_div(s->d.ny, TY));
+    dim3 block(32, SW_BLOCK_Y);
+    sw_fused_kernel<T, TX, TY><<<grid, block, smem, s->stream>>>(s->d, s->H, eta_in, u_in, v_in,
+                                                                   eta_out, u_out, v_out);
+    return cudaGetLastError();
+}
+
+// One launch of depth T from buffer `cur` into the other buffer set.
+cudaError_t sw_launch(gbsw_sw *s, int T)
+{
+    const int a = s->cur, b = 1 - s->cur;
+    cudaError_t e;
+    switch (T) {
+    case 1: e = launch_fused<1, 64, 16>(s, s->eta[a], s->u[a], s->v[a], s->eta[b], s->u[b], s->v[b]); break;
+    case 2: e = launch_fused<2, 64, 32>(s, s->eta[a], s->u[a], s->v[a], s->eta[b], s->u[b], s->v[b]); break;
+    case 3: e = launch_fused<3, 64, 32>(s, s->eta[a], s->u[a], s->v[a], s->eta[b], s->u[b], s->v[b]); break;
+    case 4: e = launch_fused<4, 64, 32>(s, s->eta[a], s->u[a], s->v[a], s->eta[b], s->u[b], s->v[b]); break;
+    default: return cudaErrorInvalidValue;
+    }
+    if (e == cudaSuccess) s->cur = b;
+    return e;
+}
+
+int auto_blocking(const gbsw_sw *) { return 4; }
+
+}  // namespace
+
+extern "C" {
+
+gbsw_status sw_create(const gbsw_sw_params *params, const double *H, const double *eta0, void *stream,
+                      gbsw_sw **out)
+{
+    if (!params || !H || !eta0 || !out) return GBSW_ERR_ARG;
+    const gbsw_sw_params P = *params;
+    if (P.nx < 2 || P.ny < 2 || P.nx > (1 << 20) || P.ny > (1 << 20)) return GBSW_ERR_ARG;
+    if (!(P.dx > 0) || !(P.dy > 0) || !(P.dt > 0) || !(P.g > 0) || !(P.eps >= 0 && P.eps <= 1) ||
+        !(P.hmin >= 0))
+        return GBSW_ERR_ARG;
+    const size_t n = (size_t)P.nx * (size_t)P.ny;
+    std::vector<float> h32(n), e32(n);
+    double hmax = 0.0;
+    for (size_t k = 0; k < n; ++k) {
+        if (!std::isfinite(H[k]) || !std::isfinite(eta0[k])) return GBSW_ERR_ARG;
+        double e = eta0[k] < -H[k] ? -H[k] : eta0[k];
+        hmax = std::max(hmax, H[k] + e);
+        h32[k] = (float)H[k];
+        e32[k] = (float)e;
+    }
+    const double courant = sqrt(P.g * hmax) * P.dt * sqrt(1.0 / (P.dx * P.dx) + 1.0 / (P.dy * P.dy));
+    if (courant > 1.0) return GBSW_ERR_CFL;
+
+    gbsw_sw *s = (gbsw_sw *)calloc(1, sizeof(gbsw_sw));
+    if (!s) return GBSW_ERR_OOM;
+    s->p = P;
+    s->stream = (cudaStream_t)stream;
+    s->d.nx = P.nx;
+    s->d.ny = P.ny;
+    s->d.pitch = (int)round_up((size_t)P.nx, 32);
+    s->d.gdt_dx = (float)(P.g * P.dt / P.dx);
+    s->d.gdt_dy = (float)(P.g * P.dt / P.dy);
+    s->d.dt_dx = (float)(P.dt / P.dx);
+    s->d.dt_dy = (float)(P.dt / P.dy);
+    s->d.q = (float)(0.25 * P.eps);
+    s->d.hmin = (float)P.hmin;
+
+    const size_t bytes = (size_t)s->d.pitch * (size_t)P.ny * sizeof(float);
+    auto fail = [&](gbsw_status code) {
+        sw_destroy(s);
+        return code;
+    };
+#define SW_ALLOC(ptr, sz)                                                      \
+    do {                                                                       \
+        cudaError_t _e = cudaMalloc((void **)&(ptr), (sz));                    \
+        if (_e != cudaSuccess) {                                               \
+            record_cuda_error(_e, "cudaMalloc", __FILE__, __LINE__);           \
+            return fail(GBSW_ERR_OOM);                                         \
+        }                                                                      \
+    } while (0)
+    SW_ALLOC(s->H, bytes);
+    for (int b = 0; b < 2; ++b) {
+        SW_ALLOC(s->eta[b], bytes);
+        SW_ALLOC(s->u[b], bytes);
+        SW_ALLOC(s->v[b], bytes);
+    }
+    SW_ALLOC(s->partials, SW_VOL_BLOCKS * 3 * sizeof(double));
+    SW_ALLOC(s->result, 3 * sizeof(double));
+    SW_ALLOC(s->wet, n);
+#undef SW_ALLOC
+    if (cudaMallocHost((void **)&s->h_result, 3 * sizeof(double)) != cudaSuccess) return fail(GBSW_ERR_OOM);
+
+    cudaError_t e = cudaSuccess;
+    float *all[7] = {s->H, s->eta[0], s->eta[1], s->u[0], s->u[1], s->v[0], s->v[1]};
+    for (float *ptr : all)
+        if (e == cudaSuccess) e = cudaMemsetAsync(ptr, 0, bytes, s->stream);
+    const size_t dp = (size_t)s->d.pitch * sizeof(float), hp = (size_t)P.nx * sizeof(float);
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(s->H, dp, h32.data(), hp, hp, P.ny, cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(s->eta[0], dp, e32.data(), hp, hp, P.ny, cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) {
+        record_cuda_error(e, "sw_create upload", __FILE__, __LINE__);
+        return fail(GBSW_ERR_CUDA);
+    }
+    *out = s;
+    return GBSW_OK;
+}
+
+gbsw_status sw_set_blocking(gbsw_sw *s, int steps_per_launch)
+{
+    if (!s || steps_per_launch < 0 || steps_per_launch > SW_MAX_BLOCKING) return GBSW_ERR_ARG;
+    s->blocking = steps_per_launch;
+    return GBSW_OK;
+}
+
+gbsw_status sw_step(gbsw_sw *s, int nsteps)
+{
+    if (!s || nsteps < 0) return GBSW_ERR_ARG;
+    const int T = s->blocking > 0 ? s->blocking : auto_blocking(s);
+    int left = nsteps;
+    while (left > 0) {
+        int t = std::min(left, T);
+        cudaError_t e = sw_launch(s, t);
+        if (e != cudaSuccess) {
+            record_cuda_error(e, "sw_fused_kernel", __FILE__, __LINE__);
+            return GBSW_ERR_CUDA;
+        }
+        left -= t;
+    }
+    return GBSW_OK;
+}
+
+gbsw_status sw_volume(gbsw_sw *s, double *volume, double *wet_volume)
+{
+    if (!s) return GBSW_ERR_ARG;
+    sw_volume_partial_kernel<<<SW_VOL_BLOCKS, SW_VOL_THREADS, 0, s->stream>>>(s->d, s->H, s->eta[s->cur],
+                                                                             s->partials);
+    GBSW_LAUNCH_CHECK();
+    sw_volume_final_kernel<<<1, SW_VOL_THREADS, 0, s->stream>>>(s->partials, SW_VOL_BLOCKS,
+                                                               s->p.dx * s->p.dy, s->result);
+    GBSW_LAUNCH_CHECK();
+    GBSW_CUDA_TRY(cudaMemcpyAsync(s->h_result, s->result, 3 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    GBSW_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    if (volume) *volume = s->h_result[0];
+    if (wet_volume) *wet_volume = s->h_result[1];
+    return s->h_result[2] != 0.0 ? GBSW_ERR_NONFINITE : GBSW_OK;
+}
+
+gbsw_status sw_get_state(gbsw_sw *s, float *eta, float *u, float *v, uint8_t *wet)
+{
+    if (!s) return GBSW_ERR_ARG;
+    const int nx = s->p.nx, ny = s->p.ny;
+    const size_t dp = (size_t)s->d.pitch * sizeof(float);
+    const size_t row = (size_t)nx * sizeof(float);
+    const int c = s->cur;
+    if (eta)
+        GBSW_CUDA_TRY(cudaMemcpy2DAsync(eta, row, s->eta[c], dp, row, ny, cudaMemcpyDeviceToHost, s->stream));
+    if (u)
+        GBSW_CUDA_TRY(cudaMemcpy2DAsync(u + 1, row + sizeof(float), s->u[c], dp, row, ny,
+                                        cudaMemcpyDeviceToHost, s->stream));
+    if (v)
+        GBSW_CUDA_TRY(cudaMemcpy2DAsync(v + nx, row, s->v[c], dp, row, ny, cudaMemcpyDeviceToHost, s->stream));
+    if (wet) {
+        dim3 block(32, 8), grid(ceil_div(nx, 32), ceil_div(ny, 8));
+        sw_wet_mask_kernel<<<grid, block, 0, s->stream>>>(s->d, s->H, s->eta[c], s->wet);
+        GBSW_LAUNCH_CHECK();
+        GBSW_CUDA_TRY(cudaMemcpyAsync(wet, s->wet, (size_t)nx * ny, cudaMemcpyDeviceToHost, s->stream));
+    }
+    GBSW_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    if (u)
+        for (int j = 0; j < ny; ++j) u[(size_t)j * (nx + 1)] = 0.0f;
+    if (v)
+        for (int i = 0; i < nx; ++i) v[i] = 0.0f;
+    return GBSW_OK;
+}
+
+gbsw_status sw_set_state(gbsw_sw *s, const float *eta, const float *u, const float *v)
+{
+    if (!s) return GBSW_ERR_ARG;
+    const int nx = s->p.nx, ny = s->p.ny;
+    const size_t dp = (size_t)s->d.pitch * sizeof(float);
+    const size_t row = (size_t)nx * sizeof(float);
+    const int c = s->cur;
+    if (eta)
+        GBSW_CUDA_TRY(cudaMemcpy2DAsync(s->eta[c], dp, eta, row, row, ny, cudaMemcpyHostToDevice, s->stream));
+    if (u) {
+        // host columns 1..nx are the faces the device stores; the east wall is forced to 0
+        GBSW_CUDA_TRY(cudaMemcpy2DAsync(s->u[c], dp, u + 1, row + sizeof(float), row, ny,
+                                        cudaMemcpyHostToDevice, s->stream));
+        GBSW_CUDA_TRY(cudaMemset2DAsync(s->u[c] + (nx - 1), dp, 0, sizeof(float), ny, s->stream));
+    }
+    if (v) {
+        GBSW_CUDA_TRY(cudaMemcpy2DAsync(s->v[c], dp, v + nx, row, row, ny, cudaMemcpyHostToDevice, s->stream));
+        GBSW_CUDA_TRY(cudaMemsetAsync(s->v[c] + (size_t)(ny - 1) * s->d.pitch, 0, row, s->stream));
+    }
+    GBSW_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    return GBSW_OK;
+}
+
+void sw_destroy(gbsw_sw *s)
+{
+    if (!s) return;
+    cudaStreamSynchronize(s->stream);
+    cudaFree(s->H);
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(s->eta[b]);
+        cudaFree(s->u[b]);
+        cudaFree(s->v[b]);
+    }
+    cudaFree(s->partials);
+    cudaFree(s->result);
+    cudaFree(s->wet);
+    if (s->h_result) cudaFreeHost(s->h_result);
+    free(s);
+}
+
+}  // extern "C"
