@@ -123,6 +123,35 @@ gbsw_status sw_set_blocking(gbsw_sw *sw, int steps_per_launch);
 /* Release the context and its device memory.  NULL is ignored. */
 void sw_destroy(gbsw_sw *sw);
 
+/*
+ * Volume reduction that allocates no memory.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc, such as applications whose own memory pool owns the whole
+ * device, or latency-critical loops where an allocation (which may
+ * synchronise the device) or an out-of-memory failure mid-run is not
+ * acceptable.
+ *
+ * Computes what sw_volume computes, on caller-owned device fields:
+ *   H, eta  device, ny rows of `pitch` floats (pitch >= nx), cell (i, j)
+ *           at j*pitch + i; read only.
+ *   out     device, 3 doubles written: dx*dy*sum(H + eta), the same over
+ *           wet cells (H + eta > hmin, FP32 test), and the count of
+ *           non-finite eta values.
+ * Sizes: 1 <= nx, ny <= 1048576, otherwise GBSW_ERR_ARG; NULL pointers or
+ * non-positive dx, dy are GBSW_ERR_ARG.  Asynchronous on `stream`; the
+ * result is bitwise equal to sw_volume's for the same fields.
+ *
+ * The partial sums live in a fixed 24 KB array inside the library (one
+ * per GPU, held until the process exits), so no call allocates anything.
+ * The first call on a device looks up that array's device address (a
+ * one-time set-up with that device current); make that first call before
+ * any stream capture.  All calls share the array and each call overwrites
+ * it completely: calls whose kernels can overlap on the GPU (other streams
+ * or host threads) race and must be serialised by the caller.
+ */
+gbsw_status sw_volume_noalloc(int nx, int ny, int pitch, double dx, double dy, double hmin,
+                              const float *H, const float *eta, double *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

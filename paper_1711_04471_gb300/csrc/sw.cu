@@ -263,3 +263,70 @@ void sw_destroy(gbsw_sw *s)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Volume reduction that allocates nothing (sw_volume_noalloc).
+//
+// Some callers cannot call cudaMalloc: applications whose memory pool owns
+// the whole device and hands out no raw allocations, and latency-critical
+// loops in which a cudaMalloc/cudaFree (which may synchronise the device)
+// or an out-of-memory failure in the middle of a run is not acceptable.
+// For them the two-pass FP64 volume reduction keeps its per-block partial
+// sums in the file-scope array below instead of in context-owned memory.
+// The array is SW_VOL_BLOCKS * 3 doubles (24 KB); every GPU that loads the
+// library holds it until the process exits.  Each call overwrites all of
+// it before reading it, so nothing has to be cleared between calls, but
+// all calls share it: calls whose kernels overlap on the GPU (different
+// streams, or different host threads) race on it.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+static __device__ __align__(256) double g_sw_volume_scratch[SW_VOL_BLOCKS * 3];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mutex;
+double *g_scratch_addr[kMaxDevices];  // device address of g_sw_volume_scratch, per device
+
+// Device address of the scratch array on the current device, looked up
+// once per device.  In host code the array's name is only a host-side
+// stand-in, so the address must come from cudaGetSymbolAddress.
+gbsw_status volume_scratch(double **out)
+{
+    int dev = 0;
+    GBSW_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return GBSW_ERR_ARG;
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    if (!g_scratch_addr[dev]) {
+        void *p = nullptr;
+        GBSW_CUDA_TRY(cudaGetSymbolAddress(&p, g_sw_volume_scratch));
+        g_scratch_addr[dev] = (double *)p;
+    }
+    *out = g_scratch_addr[dev];
+    return GBSW_OK;
+}
+
+}  // namespace
+
+extern "C" gbsw_status sw_volume_noalloc(int nx, int ny, int pitch, double dx, double dy, double hmin,
+                                         const float *H, const float *eta, double *out, void *stream)
+{
+    if (nx < 1 || ny < 1 || nx > SW_NOALLOC_MAX_SIDE || ny > SW_NOALLOC_MAX_SIDE || pitch < nx)
+        return GBSW_ERR_ARG;
+    if (!H || !eta || !out || !(dx > 0) || !(dy > 0) || !(hmin >= 0)) return GBSW_ERR_ARG;
+    double *scratch = nullptr;
+    gbsw_status st = volume_scratch(&scratch);
+    if (st != GBSW_OK) return st;
+    SWDev d = {};
+    d.nx = nx;
+    d.ny = ny;
+    d.pitch = pitch;
+    d.hmin = (float)hmin;
+    cudaStream_t s = (cudaStream_t)stream;
+    sw_volume_partial_kernel<<<SW_VOL_BLOCKS, SW_VOL_THREADS, 0, s>>>(d, H, eta, scratch);
+    GBSW_LAUNCH_CHECK();
+    sw_volume_final_kernel<<<1, SW_VOL_THREADS, 0, s>>>(scratch, SW_VOL_BLOCKS, dx * dy, out);
+    GBSW_LAUNCH_CHECK();
+    return GBSW_OK;
+}

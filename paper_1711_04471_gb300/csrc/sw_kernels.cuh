@@ -25,6 +25,7 @@ constexpr int SW_BLOCK_Y = 8;        // blocks are 32 x 8 threads
 constexpr int SW_MAX_BLOCKING = 4;   // deepest temporal blocking compiled
 constexpr int SW_VOL_BLOCKS = 1024;  // fixed, so the FP64 sum order is fixed
 constexpr int SW_VOL_THREADS = 256;
+constexpr int SW_NOALLOC_MAX_SIDE = 1 << 20;  // largest nx, ny accepted by sw_volume_noalloc
 
 template <int T, int TX, int TY>
 struct SWTile {
