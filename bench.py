@@ -184,7 +184,7 @@ def run_gbsw(args, rank, world, local):
     sw = SW(inp.params(), inp.H, inp.eta0, stream=stream)
     if args.blocking:
         sw.set_blocking(args.blocking)
-    T = args.blocking or 4
+    T = args.blocking or 3
     launches_per_step = math.ceil(STEPS_PER_BENCH_STEP / T) + 2
 
     # ---- device-resident throughput (value) ----
@@ -255,7 +255,7 @@ def run_gbsw(args, rank, world, local):
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": peak, "unit": "GB/s",
                      "frac": achieved_gbs / peak, "traffic": args.traffic,
-                     "peak_kind": peak_kind, "kernel": "sw_fused_kernel",
+                     "peak_kind": peak_kind, "kernel": "sw_stream_kernel",
                      "per_unit": f"{BYTES_PER_CELL_UPDATE} B/cell-update x {T} steps x {cells} cells per launch",
                      "compulsory_gbs": compulsory_gbs, "compulsory_frac": compulsory_gbs / peak,
                      "launch_ms": fused_launch_ms},

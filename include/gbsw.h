@@ -117,7 +117,7 @@ gbsw_status sw_get_state(gbsw_sw *sw, float *eta, float *u, float *v, uint8_t *w
 gbsw_status sw_set_state(gbsw_sw *sw, const float *eta, const float *u, const float *v);
 
 /* Number of time steps fused per kernel launch (temporal blocking depth):
- * 0 = automatic, else 1..4. */
+ * 0 = automatic, else 1..6. */
 gbsw_status sw_set_blocking(gbsw_sw *sw, int steps_per_launch);
 
 /* Release the context and its device memory.  NULL is ignored. */

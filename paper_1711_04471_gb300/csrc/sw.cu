@@ -2,10 +2,8 @@
 // "dyn", the first-order Shapiro filter "shapiro" and the state update),
 // as one fused, temporally blocked CUDA kernel, plus the FP64 volume
 // reduction.  The three map kernels the paper's compiler generates for this
-// loop are fused here into one pass over a shared-memory tile: each launch
-// loads eta, H, u, v once for a TX x TY tile plus a halo of 2*T cells, runs
-// T time steps in shared memory (the valid region shrinks by 2 cells per
-// step, the radius of one step's dependency cone) and writes the tile back.
+// loop are fused into one streaming kernel (sw_stream.cuh) that reads the
+// state once and writes it once per T time steps.
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -15,6 +13,7 @@
 
 #include "common.cuh"
 #include "sw_kernels.cuh"
+#include "sw_stream.cuh"
 
 using namespace gbsw;
 
@@ -34,22 +33,28 @@ struct gbsw_sw {
 
 namespace {
 
-template <int T, int TX, int TY>
-cudaError_t launch_fused(const gbsw_sw *s, const float *eta_in, const float *u_in, const float *v_in,
-                         float *eta_out, float *u_out, float *v_out)
+// Streaming launch of depth T: one wave of CTAs sized from the occupancy so
+// that every resident CTA gets one (strip, row segment) of equal height.
+template <int T>
+cudaError_t launch_stream(const gbsw_sw *s, const float *eta_in, const float *u_in, const float *v_in,
+                          float *eta_out, float *u_out, float *v_out)
 {
-    constexpr size_t smem = SWTile<T, TX, TY>::smem_bytes;
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(sw_fused_kernel<T, TX, TY>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sw_stream_kernel<T>, SWS_THREADS, 0);
         if (e != cudaSuccess) return e;
-        configured = true;
+        if (per_sm < 1) per_sm = 1;
     }
-    dim3 grid(ceil_div(s->d.nx, TX), ceil_div(s->d.ny, TY));
-    dim3 block(32, SW_BLOCK_Y);
-    sw_fused_kernel<T, TX, TY><<<grid, block, smem, s->stream>>>(s->d, s->H, eta_in, u_in, v_in,
-                                                                   eta_out, u_out, v_out);
+    constexpr int W = SWS_THREADS - 4 * T;
+    const int strips = ceil_div(s->d.nx, W);
+    const int capacity = per_sm * sm_count();
+    int segments = std::max(1, capacity / strips);
+    segments = std::min(segments, std::max(1, s->d.ny / (8 * T)));  // keep segments >> the pipeline depth
+    const int rows = ceil_div(s->d.ny, segments);
+    segments = ceil_div(s->d.ny, rows);
+    dim3 grid(strips, segments);
+    sw_stream_kernel<T><<<grid, SWS_THREADS, 0, s->stream>>>(s->d, rows, s->H, eta_in, u_in, v_in, eta_out,
+                                                            u_out, v_out);
     return cudaGetLastError();
 }
 
@@ -58,18 +63,22 @@ cudaError_t sw_launch(gbsw_sw *s, int T)
 {
     const int a = s->cur, b = 1 - s->cur;
     cudaError_t e;
+    const float *ei = s->eta[a], *ui = s->u[a], *vi = s->v[a];
+    float *eo = s->eta[b], *uo = s->u[b], *vo = s->v[b];
     switch (T) {
-    case 1: e = launch_fused<1, 64, 16>(s, s->eta[a], s->u[a], s->v[a], s->eta[b], s->u[b], s->v[b]); break;
-    case 2: e = launch_fused<2, 64, 32>(s, s->eta[a], s->u[a], s->v[a], s->eta[b], s->u[b], s->v[b]); break;
-    case 3: e = launch_fused<3, 64, 32>(s, s->eta[a], s->u[a], s->v[a], s->eta[b], s->u[b], s->v[b]); break;
-    case 4: e = launch_fused<4, 64, 32>(s, s->eta[a], s->u[a], s->v[a], s->eta[b], s->u[b], s->v[b]); break;
+    case 1: e = launch_stream<1>(s, ei, ui, vi, eo, uo, vo); break;
+    case 2: e = launch_stream<2>(s, ei, ui, vi, eo, uo, vo); break;
+    case 3: e = launch_stream<3>(s, ei, ui, vi, eo, uo, vo); break;
+    case 4: e = launch_stream<4>(s, ei, ui, vi, eo, uo, vo); break;
+    case 5: e = launch_stream<5>(s, ei, ui, vi, eo, uo, vo); break;
+    case 6: e = launch_stream<6>(s, ei, ui, vi, eo, uo, vo); break;
     default: return cudaErrorInvalidValue;
     }
     if (e == cudaSuccess) s->cur = b;
     return e;
 }
 
-int auto_blocking(const gbsw_sw *) { return 4; }
+int auto_blocking(const gbsw_sw *) { return 3; }
 
 }  // namespace
 

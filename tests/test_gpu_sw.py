@@ -52,7 +52,7 @@ def run_both(SW, inp, nsteps, blocking=0):
     return o, st, vol
 
 
-@pytest.mark.parametrize("blocking", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("blocking", [0, 1, 2, 3, 4, 5, 6])
 def test_hump_1000_steps(SW, blocking):
     """100x100 flat basin with the 1 m hump, 1000 steps."""
     inp = inputs.sw_hump()
