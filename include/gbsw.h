@@ -123,6 +123,112 @@ gbsw_status sw_set_blocking(gbsw_sw *sw, int steps_per_launch);
 /* Release the context and its device memory.  NULL is ignored. */
 void sw_destroy(gbsw_sw *sw);
 
+/* ------------------------------------------------------------------------
+ * Urban LES (Sec. 6.3.1: each step runs velnw, bondv1, velfg, feedbf, les,
+ * adam and press, in that order).
+ *
+ * Grid: nx*ny*nz cubic cells of size dx; u on east faces (x = 0 inflow
+ * plane, x = nx*dx outflow plane), v on north faces (periodic in y), w on
+ * top faces (ground and lid closed); pressure at centres.  Per step:
+ *   velnw : u = u* - dt grad p (previous pressure; p = 0 on the outflow face)
+ *   bondv1: inflow u = u_ref ln(z/z0)/ln(z_ref/z0), v = w = 0 at the inflow,
+ *           zero gradient at the outflow, periodic in y, no slip at the
+ *           ground, free slip at the lid
+ *   velfg : F = -div(u u) (flux form, second-order central)
+ *   feedbf: faces touching a building cell: G += dt u, F += alpha G + beta u
+ *           (Goldstein feedback forcing)
+ *   les   : nu_t = (cs dx)^2 sqrt(2 S:S); F += div(2 (nu + nu_t) S)
+ *   adam  : u* = u + dt (3/2 F - 1/2 F_old) (forward Euler on step 0)
+ *   press : A p = div(u*)/dt by red-black SOR (relaxation omega) from the
+ *           previous pressure, until ||b - A p||_2 <= tol ||b||_2 (FP64
+ *           norm, tested on the device every check_every iterations) or
+ *           max_iter iterations.  A: 7-point Laplacian, Neumann at the
+ *           inflow, ground and lid, Dirichlet p = 0 at the outflow face,
+ *           periodic in y.
+ * Velocities and the SOR sweeps are FP32; the pressure itself is kept in
+ * FP64 (the sweeps iterate on an FP32 correction that is folded into it at
+ * every residual check, which leaves the SOR iterates unchanged in exact
+ * arithmetic).
+ * ---------------------------------------------------------------------- */
+
+typedef struct gbsw_les gbsw_les;
+
+typedef struct {
+    int nx, ny, nz;         /* cells; ny even (red-black colouring is periodic in y); each >= 2 */
+    double dx;              /* cell size (m) */
+    double dt;              /* time step (s) */
+    double u_ref, z_ref;    /* inflow speed u_ref (m/s) at height z_ref (m) */
+    double z0;              /* roughness length (m), 0 < z0 < dx/2 */
+    double cs;              /* Smagorinsky constant (e.g. 0.1) */
+    double nu;              /* molecular viscosity (m^2/s) */
+    double alpha, beta;     /* Goldstein gains (s^-2, s^-1), both <= 0 */
+    double omega;           /* SOR relaxation, 0 < omega < 2 */
+    double tol;             /* relative residual target */
+    int max_iter;           /* SOR iteration cap per step */
+    int check_every;        /* iterations between FP64 residual checks, 1..1000 */
+} gbsw_les_params;
+
+typedef struct {
+    int iters;              /* SOR iterations (a multiple of check_every) */
+    int status;             /* GBSW_OK, GBSW_NOT_CONVERGED or an error */
+    double rel_res;         /* final ||b - A p|| / ||b|| */
+    float ms_predictor;     /* device time of velnw .. rhs */
+    float ms_solve;         /* device time of the pressure solve */
+} gbsw_les_stats;
+
+/* Field ids for les_get_field / les_set_field.  Every field is exchanged
+ * in the padded layout (nz+2) x (ny+2) x (nx+2), x fastest, ghost layer
+ * included; GBSW_LES_P is FP64, all others FP32.  U, V, W are the
+ * predicted velocity u* that the next step projects. */
+enum {
+    GBSW_LES_U = 0, GBSW_LES_V = 1, GBSW_LES_W = 2, GBSW_LES_P = 3,
+    GBSW_LES_FU_OLD = 4, GBSW_LES_FV_OLD = 5, GBSW_LES_FW_OLD = 6,
+    GBSW_LES_GU = 7, GBSW_LES_GV = 8, GBSW_LES_GW = 9,
+    GBSW_LES_NUT = 10, GBSW_LES_B = 11
+};
+
+/*
+ * Create an LES context.  solid: host nz*ny*nx bytes (1 = building cell),
+ * or NULL for none.  Initial state: u* = inflow profile on every x-face
+ * that touches no building (0 on those that do), v* = w* = 0, p = 0.
+ * GBSW_ERR_CFL if u_max dt/dx > 0.5 for the inflow profile.  Synchronous.
+ */
+gbsw_status les_create(const gbsw_les_params *params, const uint8_t *solid, void *stream, gbsw_les **out);
+
+/*
+ * Advance nsteps steps.  stats: host array of nsteps records or NULL.
+ * Synchronises at the end; returns the worst per-step status
+ * (GBSW_NOT_CONVERGED if any solve stopped at max_iter).
+ */
+gbsw_status les_step(gbsw_les *les, int nsteps, gbsw_les_stats *stats);
+
+/* Copy one field to / from a host buffer (layout above).  Synchronous. */
+gbsw_status les_get_field(gbsw_les *les, int field, void *host);
+gbsw_status les_set_field(gbsw_les *les, int field, const void *host);
+
+/* Steps taken so far (step 0 uses forward Euler); settable for restarts. */
+gbsw_status les_get_step(gbsw_les *les, int *step);
+gbsw_status les_set_step(gbsw_les *les, int step);
+
+/* Change the SOR parameters of later steps. */
+gbsw_status les_set_solver(gbsw_les *les, double omega, double tol, int max_iter, int check_every);
+
+void les_destroy(gbsw_les *les);
+
+/*
+ * Stand-alone pressure solve with the operator of les_step.
+ *   p  device, nz*ny*nx FP32 (x fastest): initial guess in, solution out
+ *   b  device, nz*ny*nx FP32 right-hand side
+ * Both are caller-owned.  ny must be even.  Iterations are counted in
+ * multiples of check_every.  Synchronous on `stream`; returns GBSW_OK when
+ * ||b - A p|| <= tol ||b|| (or ||b|| < 1e-30, with 0 iterations),
+ * GBSW_NOT_CONVERGED at max_iter.  *iters and *rel_res may be NULL.
+ * Allocates and frees its own workspace (FP64 pressure, FP32 correction
+ * and residual).
+ */
+gbsw_status poisson_solve(int nx, int ny, int nz, double dx, float *p, const float *b, double omega, double tol,
+                          int max_iter, int check_every, void *stream, int *iters, double *rel_res);
+
 /*
  * Volume reduction that allocates no memory.  The paper has no
  * counterpart: this entry point exists for callers that cannot call

@@ -1,8 +1,31 @@
-"""Declarations of the later-added C-ABI entry points (see include/gbsw.h)."""
+"""ctypes declarations of the LES, Poisson and later entry points of
+include/gbsw.h (the 2DSW ones are in _native.py)."""
 import ctypes as C
 
 
+class LESParams(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("dx", C.c_double), ("dt", C.c_double),
+                ("u_ref", C.c_double), ("z_ref", C.c_double), ("z0", C.c_double), ("cs", C.c_double),
+                ("nu", C.c_double), ("alpha", C.c_double), ("beta", C.c_double), ("omega", C.c_double),
+                ("tol", C.c_double), ("max_iter", C.c_int), ("check_every", C.c_int)]
+
+
+class LESStats(C.Structure):
+    _fields_ = [("iters", C.c_int), ("status", C.c_int), ("rel_res", C.c_double), ("ms_predictor", C.c_float),
+                ("ms_solve", C.c_float)]
+
+
 def declare(L, sig):
-    vp, fp, dp = C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_double)
+    vp, ip, dp = C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_double)
     sig(L, "sw_volume_noalloc", C.c_int,
         [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, vp, vp, vp, vp])
+    sig(L, "les_create", C.c_int, [C.POINTER(LESParams), vp, vp, C.POINTER(vp)])
+    sig(L, "les_step", C.c_int, [vp, C.c_int, C.POINTER(LESStats)])
+    sig(L, "les_get_field", C.c_int, [vp, C.c_int, vp])
+    sig(L, "les_set_field", C.c_int, [vp, C.c_int, vp])
+    sig(L, "les_get_step", C.c_int, [vp, ip])
+    sig(L, "les_set_step", C.c_int, [vp, C.c_int])
+    sig(L, "les_set_solver", C.c_int, [vp, C.c_double, C.c_double, C.c_int, C.c_int])
+    sig(L, "les_destroy", None, [vp])
+    sig(L, "poisson_solve", C.c_int, [C.c_int, C.c_int, C.c_int, C.c_double, vp, vp, C.c_double, C.c_double,
+                                      C.c_int, C.c_int, vp, ip, dp])

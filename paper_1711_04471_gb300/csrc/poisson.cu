@@ -1,0 +1,397 @@
+// Red-black SOR pressure solve ("press", Sec. 6.3.1 of arXiv:1711.04471)
+// with an FP64 residual norm and a device-side convergence test: one solve
+// is one launch of a CUDA graph whose while-node repeats
+// [m SOR iterations, FP64 residual, test] until ||b - A p|| <= tol ||b||
+// or max_iter, with no host round trip.
+#include <math.h>
+#include <stdlib.h>
+
+#include <algorithm>
+
+#include "poisson.cuh"
+
+namespace gbsw {
+
+__device__ __forceinline__ long long pidx(const PDims &d, int i, int j, int k)
+{
+    return (long long)k * d.plane + (long long)j * d.pitch + i;
+}
+
+// Slot of cell (i, j, k) in the array of its colour.
+__device__ __forceinline__ long long cidx(const PDims &d, int i, int j, int k)
+{
+    return (long long)k * d.cplane + (long long)j * d.cpitch + 1 + ((i - 1) >> 1);
+}
+
+__device__ __forceinline__ float pdiag(const PDims &d, int i, int k)
+{
+    return 6.0f - (i == 1) - (k == 1) - (k == d.nz) + (i == d.nx);
+}
+
+// One colour half-sweep over cells with (i + j + k) % 2 == colour; thread
+// (slot, j, k) owns the cell of that colour at slot `slot` of row (j, k).
+// FIRST: first iteration after a residual check; the correction restarts
+// from 0 (the old correction is folded into p_hi first).
+// Launch: grid (ceil(((nx+1)/2) / 128), ny, nz), block 128.
+template <bool FIRST>
+__global__ void __launch_bounds__(128)
+sor_sweep_kernel(PDims d, int colour, float omega, float h2, float *__restrict__ ec, const float *__restrict__ eo,
+                 const float *__restrict__ rc, double *__restrict__ p_hi)
+{
+    const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y + 1, k = blockIdx.z + 1;
+    const int q = (colour + 1 + j + k) & 1;
+    const int i = 2 * slot + 1 + q;
+    if (i > d.nx) return;
+    const long long c = (long long)k * d.cplane + (long long)j * d.cpitch + 1 + slot;
+    float e_old = 0.0f;
+    if (FIRST) {
+        p_hi[pidx(d, i, j, k)] += (double)ec[c];
+    } else {
+        e_old = ec[c];
+    }
+    float s = 0.0f;
+    if (!FIRST || colour == 1) {  // on the first red half-sweep every neighbour is still 0
+        const int jm = (j == 1) ? d.ny : j - 1;
+        const int jp = (j == d.ny) ? 1 : j + 1;
+        const long long row = (long long)k * d.cplane;
+        s = (eo[c - 1 + q] + eo[c + q]) +
+            (eo[row + (long long)jm * d.cpitch + 1 + slot] + eo[row + (long long)jp * d.cpitch + 1 + slot]) +
+            (eo[c - d.cplane] + eo[c + d.cplane]);
+    }
+    ec[c] = e_old + omega * ((s - h2 * rc[c]) / pdiag(d, i, k) - e_old);
+}
+
+// r = b - A (p_hi + e) in FP64 (stored as FP32 in the colour arrays), with
+// block partial sums of ||r||^2 and ||b||^2.  Grid-stride over the interior
+// with a fixed grid.
+__global__ void __launch_bounds__(POI_RED_THREADS)
+poisson_resid_kernel(PDims d, const float *__restrict__ b, const double *__restrict__ p_hi,
+                     const float *__restrict__ e0, const float *__restrict__ e1, float *__restrict__ r0,
+                     float *__restrict__ r1, double *__restrict__ partials)
+{
+    __shared__ double red[POI_RED_THREADS / 32];
+    const double r2 = 1.0 / (d.dx * d.dx);
+    const long long total = (long long)d.nx * d.ny * d.nz;
+    double rr = 0.0, bb = 0.0;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(q % d.nx) + 1;
+        const long long t = q / d.nx;
+        const int j = (int)(t % d.ny) + 1;
+        const int k = (int)(t / d.ny) + 1;
+        const int jm = (j == 1) ? d.ny : j - 1;
+        const int jp = (j == d.ny) ? 1 : j + 1;
+        // p at a cell: FP64 base + FP32 correction of that cell's colour;
+        // cells outside the grid in x or z read as 0 (ghost values unused)
+        auto P = [&](int ii, int jj, int kk) -> double {
+            if (ii < 1 || ii > d.nx || kk < 1 || kk > d.nz) return 0.0;
+            const float *ea = ((ii + jj + kk) & 1) ? e1 : e0;
+            return p_hi[pidx(d, ii, jj, kk)] + (double)ea[cidx(d, ii, jj, kk)];
+        };
+        const double s = (P(i - 1, j, k) + P(i + 1, j, k)) + (P(i, jm, k) + P(i, jp, k)) +
+                         (P(i, j, k - 1) + P(i, j, k + 1));
+        const double bc = (double)b[pidx(d, i, j, k)];
+        const double res = bc - (s - (double)pdiag(d, i, k) * P(i, j, k)) * r2;
+        float *ra = ((i + j + k) & 1) ? r1 : r0;
+        ra[cidx(d, i, j, k)] = (float)res;
+        rr += res * res;
+        bb += bc * bc;
+    }
+    rr = block_sum_f64<POI_RED_THREADS / 32>(rr, red);
+    bb = block_sum_f64<POI_RED_THREADS / 32>(bb, red);
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = rr;
+        partials[2 * blockIdx.x + 1] = bb;
+    }
+}
+
+// Folds the partials (fixed order), updates the control block and sets the
+// while-node condition: continue while rho > tol and iters < max_iter.
+__global__ void __launch_bounds__(POI_RED_THREADS)
+poisson_test_kernel(const double *__restrict__ partials, int nblocks, PoissonCtl *ctl, double tol, int max_iter,
+                    int m, int counting, cudaGraphConditionalHandle handle)
+{
+    __shared__ double red[POI_RED_THREADS / 32];
+    double rr = 0.0, bb = 0.0;
+    for (int q = threadIdx.x; q < nblocks; q += blockDim.x) {
+        rr += partials[2 * q];
+        bb += partials[2 * q + 1];
+    }
+    rr = block_sum_f64<POI_RED_THREADS / 32>(rr, red);
+    bb = block_sum_f64<POI_RED_THREADS / 32>(bb, red);
+    if (threadIdx.x == 0) {
+        if (counting) {
+            ctl->iters += m;
+        } else {
+            ctl->iters = 0;
+            ctl->status = DEV_OK;
+        }
+        ctl->rr = rr;
+        ctl->bb = bb;
+        const double rho = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+        ctl->rho = rho;
+        const bool bad = !isfinite(rho);
+        if (bad) ctl->status = DEV_NONFINITE;
+        const bool done = bad || bb < 1e-60 || rho <= tol || ctl->iters >= max_iter;
+        ctl->done = done ? 1 : 0;
+        cudaGraphSetConditional(handle, done ? 0u : 1u);
+    }
+}
+
+// p_hi += e, e = 0 on the interior cells of one colour (end of a solve).
+__global__ void poisson_fold_kernel(PDims d, int colour, double *__restrict__ p_hi, float *__restrict__ ec)
+{
+    const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y + 1, k = blockIdx.z + 1;
+    const int i = 2 * slot + 1 + ((colour + 1 + j + k) & 1);
+    if (i > d.nx) return;
+    const long long c = (long long)k * d.cplane + (long long)j * d.cpitch + 1 + slot;
+    p_hi[pidx(d, i, j, k)] += (double)ec[c];
+    ec[c] = 0.0f;
+}
+
+// Dense (nz, ny, nx) <-> padded layout copies for the standalone solve.
+__global__ void poisson_scatter_kernel(PDims d, const float *__restrict__ src, float *__restrict__ dst_f,
+                                       double *__restrict__ dst_d)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y, k = blockIdx.z;
+    if (i >= d.nx) return;
+    const float v = src[((long long)k * d.ny + j) * d.nx + i];
+    const long long c = pidx(d, i + 1, j + 1, k + 1);
+    if (dst_f) dst_f[c] = v;
+    if (dst_d) dst_d[c] = (double)v;
+}
+
+__global__ void poisson_gather_kernel(PDims d, const double *__restrict__ src, float *__restrict__ dst)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y, k = blockIdx.z;
+    if (i >= d.nx) return;
+    dst[((long long)k * d.ny + j) * d.nx + i] = (float)src[pidx(d, i + 1, j + 1, k + 1)];
+}
+
+// ---------------------------------------------------------------------------
+
+gbsw_status PoissonSolver::init(int nx, int ny, int nz, double dx, const float *b_dev, cudaStream_t s)
+{
+    d.nx = nx;
+    d.ny = ny;
+    d.nz = nz;
+    d.pitch = (int)round_up((size_t)nx + 2, 32);
+    d.plane = (long long)(ny + 2) * d.pitch;
+    d.cpitch = (int)round_up((size_t)(nx >> 1) + 2, 32);
+    d.cplane = (long long)(ny + 2) * d.cpitch;
+    d.dx = dx;
+    b = b_dev;
+    stream = s;
+    const size_t n = (size_t)d.plane * (size_t)(nz + 2);
+    const size_t nc = (size_t)d.cplane * (size_t)(nz + 2);
+    GBSW_CUDA_TRY(cudaMalloc((void **)&p_hi, n * sizeof(double)));
+    GBSW_CUDA_TRY(cudaMemsetAsync(p_hi, 0, n * sizeof(double), stream));
+    for (int c = 0; c < 2; ++c) {
+        GBSW_CUDA_TRY(cudaMalloc((void **)&e[c], nc * sizeof(float)));
+        GBSW_CUDA_TRY(cudaMalloc((void **)&r[c], nc * sizeof(float)));
+        GBSW_CUDA_TRY(cudaMemsetAsync(e[c], 0, nc * sizeof(float), stream));
+        GBSW_CUDA_TRY(cudaMemsetAsync(r[c], 0, nc * sizeof(float), stream));
+    }
+    GBSW_CUDA_TRY(cudaMalloc((void **)&partials, 2 * POI_RED_BLOCKS * sizeof(double)));
+    GBSW_CUDA_TRY(cudaMalloc((void **)&ctl, sizeof(PoissonCtl)));
+    GBSW_CUDA_TRY(cudaMemsetAsync(ctl, 0, sizeof(PoissonCtl), stream));
+    dirty_ = true;
+    return GBSW_OK;
+}
+
+void PoissonSolver::release()
+{
+    if (exec_) cudaGraphExecDestroy(exec_);
+    if (graph_) cudaGraphDestroy(graph_);
+    exec_ = nullptr;
+    graph_ = nullptr;
+    cudaFree(p_hi);
+    for (int c = 0; c < 2; ++c) {
+        cudaFree(e[c]);
+        cudaFree(r[c]);
+        e[c] = r[c] = nullptr;
+    }
+    cudaFree(partials);
+    cudaFree(ctl);
+    p_hi = nullptr;
+    partials = nullptr;
+    ctl = nullptr;
+}
+
+gbsw_status PoissonSolver::configure(double omega_, double tol_, int max_iter_, int check_every)
+{
+    if (!(omega_ > 0.0 && omega_ < 2.0) || !(tol_ >= 0.0) || max_iter_ < 0 || check_every < 1 || check_every > 1000)
+        return GBSW_ERR_ARG;
+    if (omega_ != omega || tol_ != tol || max_iter_ != max_iter || check_every != m) dirty_ = true;
+    omega = omega_;
+    tol = tol_;
+    max_iter = max_iter_;
+    m = check_every;
+    return GBSW_OK;
+}
+
+gbsw_status PoissonSolver::build_graph()
+{
+    if (exec_) cudaGraphExecDestroy(exec_);
+    if (graph_) cudaGraphDestroy(graph_);
+    exec_ = nullptr;
+    graph_ = nullptr;
+
+    const size_t nc = (size_t)d.cplane * (size_t)(d.nz + 2);
+    const float om = (float)omega, h2 = (float)(d.dx * d.dx);
+    const int nxh = (d.nx + 1) / 2;
+    const dim3 sgrid(ceil_div(nxh, 128), d.ny, d.nz), sblock(128);
+
+    cudaStream_t cs = nullptr;
+    GBSW_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraphConditionalHandle handle;
+    cudaGraphNodeParams cp = {};
+    cudaGraphNode_t cnode;
+    cudaGraph_t body;
+    cudaError_t err = cudaSuccess;
+    auto chk = [&](cudaError_t e2) {
+        if (err == cudaSuccess && e2 != cudaSuccess) err = e2;
+    };
+    chk(cudaGraphCreate(&graph_, 0));
+    chk(cudaGraphConditionalHandleCreate(&handle, graph_, 0, cudaGraphCondAssignDefault));
+    chk(cudaStreamBeginCaptureToGraph(cs, graph_, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    if (err == cudaSuccess) {
+        // prelude: e = 0, r = b - A p_hi, first test
+        chk(cudaMemsetAsync(e[0], 0, nc * sizeof(float), cs));
+        chk(cudaMemsetAsync(e[1], 0, nc * sizeof(float), cs));
+        poisson_resid_kernel<<<POI_RED_BLOCKS, POI_RED_THREADS, 0, cs>>>(d, b, p_hi, e[0], e[1], r[0], r[1],
+                                                                        partials);
+        chk(cudaGetLastError());
+        poisson_test_kernel<<<1, POI_RED_THREADS, 0, cs>>>(partials, POI_RED_BLOCKS, ctl, tol, max_iter, m, 0, handle);
+        chk(cudaGetLastError());
+        // while node
+        cudaStreamCaptureStatus cst;
+        cudaGraph_t cap_graph;
+        const cudaGraphNode_t *deps = nullptr;
+        size_t ndeps = 0;
+        chk(cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cap_graph, &deps, nullptr, &ndeps));
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = handle;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        if (err == cudaSuccess) chk(cudaGraphAddNode(&cnode, cap_graph, deps, nullptr, ndeps, &cp));
+        if (err == cudaSuccess) chk(cudaStreamUpdateCaptureDependencies(cs, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+        // epilogue: fold the last correction
+        poisson_fold_kernel<<<sgrid, sblock, 0, cs>>>(d, 0, p_hi, e[0]);
+        poisson_fold_kernel<<<sgrid, sblock, 0, cs>>>(d, 1, p_hi, e[1]);
+        chk(cudaGetLastError());
+    }
+    cudaGraph_t captured = nullptr;
+    cudaError_t e_end = cudaStreamEndCapture(cs, &captured);
+    chk(e_end);
+    if (err == cudaSuccess) {
+        // body of the while node: m iterations, residual, test
+        body = cp.conditional.phGraph_out[0];
+        chk(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        if (err == cudaSuccess) {
+            sor_sweep_kernel<true><<<sgrid, sblock, 0, cs>>>(d, 0, om, h2, e[0], e[1], r[0], p_hi);
+            sor_sweep_kernel<true><<<sgrid, sblock, 0, cs>>>(d, 1, om, h2, e[1], e[0], r[1], p_hi);
+            for (int it = 1; it < m; ++it) {
+                sor_sweep_kernel<false><<<sgrid, sblock, 0, cs>>>(d, 0, om, h2, e[0], e[1], r[0], p_hi);
+                sor_sweep_kernel<false><<<sgrid, sblock, 0, cs>>>(d, 1, om, h2, e[1], e[0], r[1], p_hi);
+            }
+            poisson_resid_kernel<<<POI_RED_BLOCKS, POI_RED_THREADS, 0, cs>>>(d, b, p_hi, e[0], e[1], r[0], r[1],
+                                                                            partials);
+            poisson_test_kernel<<<1, POI_RED_THREADS, 0, cs>>>(partials, POI_RED_BLOCKS, ctl, tol, max_iter, m, 1,
+                                                              handle);
+            chk(cudaGetLastError());
+        }
+        cudaGraph_t body_out = nullptr;
+        chk(cudaStreamEndCapture(cs, &body_out));
+    }
+    if (err == cudaSuccess) chk(cudaGraphInstantiate(&exec_, graph_, 0));
+    cudaStreamDestroy(cs);
+    if (err != cudaSuccess) {
+        record_cuda_error(err, "poisson graph build", __FILE__, __LINE__);
+        return GBSW_ERR_CUDA;
+    }
+    dirty_ = false;
+    return GBSW_OK;
+}
+
+gbsw_status PoissonSolver::enqueue()
+{
+    if (dirty_) {
+        gbsw_status st = build_graph();
+        if (st != GBSW_OK) return st;
+    }
+    GBSW_CUDA_TRY(cudaGraphLaunch(exec_, stream));
+    return GBSW_OK;
+}
+
+gbsw_status PoissonSolver::record(PoissonCtl *dst)
+{
+    GBSW_CUDA_TRY(cudaMemcpyAsync(dst, ctl, sizeof(PoissonCtl), cudaMemcpyDeviceToDevice, stream));
+    return GBSW_OK;
+}
+
+}  // namespace gbsw
+
+using namespace gbsw;
+
+extern "C" gbsw_status poisson_solve(int nx, int ny, int nz, double dx, float *p, const float *b, double omega,
+                                     double tol, int max_iter, int check_every, void *stream, int *iters,
+                                     double *rel_res)
+{
+    if (nx < 2 || ny < 2 || nz < 2 || (ny & 1) || nx > 8192 || ny > 8192 || nz > 8192 || !(dx > 0) || !p || !b)
+        return GBSW_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    PoissonSolver S;
+    float *bp = nullptr;
+    gbsw_status st = GBSW_OK;
+    PoissonCtl host{};
+    do {
+        PDims d0;
+        d0.pitch = (int)round_up((size_t)nx + 2, 32);
+        d0.plane = (long long)(ny + 2) * d0.pitch;
+        const size_t np = (size_t)d0.plane * (size_t)(nz + 2);
+        cudaError_t e = cudaMalloc((void **)&bp, np * sizeof(float));
+        if (e != cudaSuccess) {
+            record_cuda_error(e, "cudaMalloc", __FILE__, __LINE__);
+            st = GBSW_ERR_OOM;
+            break;
+        }
+        if ((e = cudaMemsetAsync(bp, 0, np * sizeof(float), s)) != cudaSuccess) {
+            st = GBSW_ERR_CUDA;
+            break;
+        }
+        st = S.init(nx, ny, nz, dx, bp, s);
+        if (st != GBSW_OK) break;
+        st = S.configure(omega, tol, max_iter, check_every);
+        if (st != GBSW_OK) break;
+        const dim3 g(ceil_div(nx, 128), ny, nz), blk(128);
+        poisson_scatter_kernel<<<g, blk, 0, s>>>(S.d, b, bp, nullptr);
+        poisson_scatter_kernel<<<g, blk, 0, s>>>(S.d, p, nullptr, S.p_hi);
+        if ((e = cudaGetLastError()) != cudaSuccess) {
+            record_cuda_error(e, "poisson scatter", __FILE__, __LINE__);
+            st = GBSW_ERR_CUDA;
+            break;
+        }
+        st = S.enqueue();
+        if (st != GBSW_OK) break;
+        poisson_gather_kernel<<<g, blk, 0, s>>>(S.d, S.p_hi, p);
+        if ((e = cudaGetLastError()) != cudaSuccess ||
+            (e = cudaMemcpyAsync(&host, S.ctl, sizeof(PoissonCtl), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(s)) != cudaSuccess) {
+            record_cuda_error(e, "poisson solve", __FILE__, __LINE__);
+            st = GBSW_ERR_CUDA;
+            break;
+        }
+    } while (0);
+    S.release();
+    cudaFree(bp);
+    if (st != GBSW_OK) return st;
+    if (iters) *iters = host.iters;
+    if (rel_res) *rel_res = host.rho;
+    if (host.status != DEV_OK) return dev_status_to_gbsw(host.status);
+    return host.done && (host.rho <= tol || host.bb < 1e-60) ? GBSW_OK : GBSW_NOT_CONVERGED;
+}

@@ -1,0 +1,85 @@
+// Pressure Poisson solver of the UFLES step ("press", Sec. 6.3.1 of
+// arXiv:1711.04471: the Poisson equation for pressure solved by successive
+// over-relaxation), red-black ordered, FP32 sweeps with an FP64 outer
+// residual.
+//
+// Operator (7-point Laplacian on an nx*ny*nz cell grid of spacing dx):
+//   (A p)_c = (sum of neighbour values - d_c p_c) / dx^2,
+//   d_c = 6 - [i == 1] - [k == 1] - [k == nz] + [i == nx]
+// i.e. Neumann at the inflow plane, the ground and the lid (mirror ghost),
+// Dirichlet p = 0 on the outflow face (antisymmetric ghost), periodic in y.
+//
+// Mixed precision without changing the iteration: SOR is an affine
+// stationary method, so running it on the correction e for A e = r with
+// r = b - A p_hi from e = 0 produces p_hi + e equal (in exact arithmetic) to
+// the SOR iterates on p itself.  Every m iterations the FP64 residual
+// r = b - A (p_hi + e) and its norm are formed, and e is folded into the
+// FP64 base p_hi by the next sweep.  The sweeps move 4-byte words only; the
+// 1e-6 relative residual is reachable although FP32 storage of p alone
+// would floor it near 1e-5 for smooth pressure fields.
+//
+// Device layout.  p_hi: (nz+2) x (ny+2) x pitch FP64, interior cell
+// (i,j,k) (1-based) at k*plane + j*pitch + i.  e and r are stored split by
+// colour c = (i+j+k) mod 2: colour array c holds cell (i,j,k) of that
+// colour at k*cplane + j*cpitch + 1 + ((i-1) >> 1), so a half-sweep reads
+// its own colour and the other colour with unit stride.  Slot 0 and the
+// slots past the last cell of a row, and the y/z ghost rows, stay 0: the
+// boundary rules enter only through d_c, and y is wrapped explicitly.
+#pragma once
+
+#include "common.cuh"
+
+namespace gbsw {
+
+struct PDims {
+    int nx, ny, nz, pitch;
+    long long plane;   // (ny+2) * pitch
+    int cpitch;        // row pitch of a colour array (>= (nx >> 1) + 2)
+    long long cplane;  // (ny+2) * cpitch
+    double dx;
+};
+
+struct PoissonCtl {
+    double bb;        // ||b||^2
+    double rr;        // ||r||^2 at the last check
+    double rho;       // ||r|| / ||b||
+    int iters;        // SOR iterations done
+    int done;
+    int status;       // DEV_* code
+    int pad;
+};
+
+class PoissonSolver {
+public:
+    // b: device array in the padded layout (owned by the caller), read at
+    // every residual check.  p_hi is owned by the solver.
+    gbsw_status init(int nx, int ny, int nz, double dx, const float *b, cudaStream_t stream);
+    void release();
+    gbsw_status configure(double omega, double tol, int max_iter, int check_every);
+    // Enqueue one solve (asynchronous; one graph launch).
+    gbsw_status enqueue();
+    // Copy the control block of the last solve into *out (device -> device).
+    gbsw_status record(PoissonCtl *dev_dst);
+
+    PDims d{};
+    double *p_hi = nullptr;   // FP64 pressure (the solution)
+    float *e[2] = {};         // FP32 correction of the inner sweeps, per colour
+    float *r[2] = {};         // FP32 residual (right-hand side of the sweeps), per colour
+    const float *b = nullptr;
+    double *partials = nullptr;
+    PoissonCtl *ctl = nullptr;
+    cudaStream_t stream = nullptr;
+    double omega = 1.8, tol = 1e-6;
+    int max_iter = 100000, m = 10;
+
+private:
+    gbsw_status build_graph();
+    cudaGraph_t graph_ = nullptr;
+    cudaGraphExec_t exec_ = nullptr;
+    bool dirty_ = true;
+};
+
+constexpr int POI_RED_BLOCKS = 2048;   // fixed, so the FP64 sum order is fixed
+constexpr int POI_RED_THREADS = 256;
+
+}  // namespace gbsw

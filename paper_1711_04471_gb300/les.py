@@ -1,0 +1,102 @@
+"""Urban LES time step (Sec. 6.3 of arXiv:1711.04471) and the stand-alone
+pressure solve, on the GPU.  Thin wrapper of the les_* / poisson_solve
+entry points of libgbsw.so."""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _native as N
+from ._native_ext import LESParams, LESStats
+
+FIELDS = dict(u=0, v=1, w=2, p=3, fuo=4, fvo=5, fwo=6, gu=7, gv=8, gw=9, nut=10, b=11)
+
+DEFAULTS = dict(dx=4.0, dt=0.025, u_ref=5.0, z_ref=10.0, z0=0.1, cs=0.1, nu=1.5e-5, alpha=-100.0, beta=-10.0,
+                omega=1.8, tol=1e-6, max_iter=100000, check_every=10)
+
+
+class LES:
+    def __init__(self, nx: int, ny: int, nz: int, solid: np.ndarray | None = None, stream=None, **kw):
+        d = dict(DEFAULTS)
+        d.update(kw)
+        self.shape = (nz, ny, nx)
+        self.params = LESParams(nx, ny, nz, d["dx"], d["dt"], d["u_ref"], d["z_ref"], d["z0"], d["cs"], d["nu"],
+                                d["alpha"], d["beta"], d["omega"], d["tol"], int(d["max_iter"]),
+                                int(d["check_every"]))
+        self._solid = None if solid is None else np.ascontiguousarray(solid, dtype=np.uint8)
+        if self._solid is not None and self._solid.shape != self.shape:
+            raise ValueError("solid must be (nz, ny, nx)")
+        h = C.c_void_p()
+        sp = None if self._solid is None else self._solid.ctypes.data_as(C.c_void_p)
+        N.check(N.lib().les_create(C.byref(self.params), sp, N.stream_handle(stream), C.byref(h)), "les_create")
+        self._h = h
+
+    def step(self, nsteps: int = 1, stats: bool = True):
+        arr = (LESStats * max(1, nsteps))() if stats else None
+        st = N.lib().les_step(self._h, int(nsteps), arr)
+        N.check(st, "les_step")
+        if not stats:
+            return st
+        return [dict(iters=a.iters, status=a.status, rel_res=a.rel_res, ms_predictor=a.ms_predictor,
+                     ms_solve=a.ms_solve) for a in arr[:nsteps]]
+
+    def get(self, name: str) -> np.ndarray:
+        nz, ny, nx = self.shape
+        out = np.empty((nz + 2, ny + 2, nx + 2), dtype=np.float64 if name == "p" else np.float32)
+        N.check(N.lib().les_get_field(self._h, FIELDS[name], out.ctypes.data_as(C.c_void_p)), "les_get_field")
+        return out
+
+    def set(self, name: str, arr: np.ndarray):
+        nz, ny, nx = self.shape
+        a = np.ascontiguousarray(arr, dtype=np.float64 if name == "p" else np.float32)
+        if a.shape != (nz + 2, ny + 2, nx + 2):
+            raise ValueError("fields are exchanged in the padded (nz+2, ny+2, nx+2) layout")
+        N.check(N.lib().les_set_field(self._h, FIELDS[name], a.ctypes.data_as(C.c_void_p)), "les_set_field")
+
+    @property
+    def step_count(self) -> int:
+        s = C.c_int()
+        N.check(N.lib().les_get_step(self._h, C.byref(s)), "les_get_step")
+        return s.value
+
+    @step_count.setter
+    def step_count(self, v: int):
+        N.check(N.lib().les_set_step(self._h, int(v)), "les_set_step")
+
+    def set_solver(self, omega=None, tol=None, max_iter=None, check_every=None):
+        p = self.params
+        p.omega = p.omega if omega is None else omega
+        p.tol = p.tol if tol is None else tol
+        p.max_iter = p.max_iter if max_iter is None else int(max_iter)
+        p.check_every = p.check_every if check_every is None else int(check_every)
+        N.check(N.lib().les_set_solver(self._h, p.omega, p.tol, p.max_iter, p.check_every), "les_set_solver")
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            N.lib().les_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def poisson_solve(p, b, dx: float, omega=1.8, tol=1e-6, max_iter=100000, check_every=10, stream=None):
+    """Solve A p = b in place on CUDA float32 tensors of shape (nz, ny, nx).
+    Returns (status, iterations, relative residual)."""
+    nz, ny, nx = p.shape
+    assert b.shape == p.shape
+    it, rr = C.c_int(), C.c_double()
+    st = N.lib().poisson_solve(nx, ny, nz, dx, N.tensor_ptr(p, "float32"), N.tensor_ptr(b, "float32"), omega, tol,
+                               int(max_iter), int(check_every), N.stream_handle(stream), C.byref(it), C.byref(rr))
+    N.check(st, "poisson_solve")
+    return st, it.value, rr.value
