@@ -213,6 +213,12 @@ gbsw_status les_set_step(gbsw_les *les, int step);
 /* Change the SOR parameters of later steps. */
 gbsw_status les_set_solver(gbsw_les *les, double omega, double tol, int max_iter, int check_every);
 
+/* Paper mode (Sec. 6.3.2 runs UFLES with the number of SOR iterations set
+ * to 50): niter > 0 makes every later step run exactly niter SOR
+ * iterations with no convergence test (stats report the final residual,
+ * status GBSW_OK); 0 restores the tolerance-driven solve. */
+gbsw_status les_set_fixed_iterations(gbsw_les *les, int niter);
+
 void les_destroy(gbsw_les *les);
 
 /*
@@ -220,7 +226,8 @@ void les_destroy(gbsw_les *les);
  *   p  device, nz*ny*nx FP32 (x fastest): initial guess in, solution out
  *   b  device, nz*ny*nx FP32 right-hand side
  * Both are caller-owned.  ny must be even.  Iterations are counted in
- * multiples of check_every.  Synchronous on `stream`; returns GBSW_OK when
+ * multiples of check_every.  tol < 0 selects the fixed-count mode of the
+ * paper: exactly max_iter iterations, no convergence test, GBSW_OK.  Synchronous on `stream`; returns GBSW_OK when
  * ||b - A p|| <= tol ||b|| (or ||b|| < 1e-30, with 0 iterations),
  * GBSW_NOT_CONVERGED at max_iter.  *iters and *rel_res may be NULL.
  * Allocates and frees its own workspace (FP64 pressure, FP32 correction

@@ -290,6 +290,7 @@ struct gbsw_les {
     PoissonCtl *ctl_log;   // per-step copies of the solver control block
     int ctl_log_len;
     int step;
+    int fixed_iters;       // > 0: paper mode, exactly this many SOR iterations per step
     size_t n;              // elements per padded field
 };
 
@@ -466,7 +467,7 @@ gbsw_status les_step(gbsw_les *s, int nsteps, gbsw_les_stats *stats)
         st = les_predictor(s);
         if (st != GBSW_OK) break;
         if (stats) cudaEventRecord(ev[3 * t + 1], s->stream);
-        st = s->solver.enqueue();
+        st = s->fixed_iters > 0 ? s->solver.enqueue_fixed(s->fixed_iters) : s->solver.enqueue();
         if (st != GBSW_OK) break;
         if (stats) cudaEventRecord(ev[3 * t + 2], s->stream);
         st = s->solver.record(s->ctl_log + t);
@@ -485,7 +486,7 @@ gbsw_status les_step(gbsw_les *s, int nsteps, gbsw_les_stats *stats)
         const PoissonCtl &c = log[t];
         gbsw_status one = GBSW_OK;
         if (c.status != DEV_OK) one = dev_status_to_gbsw(c.status);
-        else if (!(c.rho <= s->p.tol || c.bb < 1e-60)) one = GBSW_NOT_CONVERGED;
+        else if (s->fixed_iters == 0 && !(c.rho <= s->p.tol || c.bb < 1e-60)) one = GBSW_NOT_CONVERGED;
         if (stats) {
             stats[t].iters = c.iters;
             stats[t].status = one;
@@ -547,6 +548,13 @@ gbsw_status les_set_step(gbsw_les *s, int step)
 {
     if (!s || step < 0) return GBSW_ERR_ARG;
     s->step = step;
+    return GBSW_OK;
+}
+
+gbsw_status les_set_fixed_iterations(gbsw_les *s, int niter)
+{
+    if (!s || niter < 0) return GBSW_ERR_ARG;
+    s->fixed_iters = niter;
     return GBSW_OK;
 }
 

@@ -28,38 +28,56 @@ __device__ __forceinline__ float pdiag(const PDims &d, int i, int k)
     return 6.0f - (i == 1) - (k == 1) - (k == d.nz) + (i == d.nx);
 }
 
-// One colour half-sweep over cells with (i + j + k) % 2 == colour; thread
-// (slot, j, k) owns the cell of that colour at slot `slot` of row (j, k).
+// One colour half-sweep over cells with (i + j + k) % 2 == colour.  Thread
+// (slot, j, kp) owns the cells of that colour at slot `slot` of rows
+// (j, 2kp+1) and (j, 2kp+2): two independent updates per thread keep more
+// loads in flight.
 // FIRST: first iteration after a residual check; the correction restarts
 // from 0 (the old correction is folded into p_hi first).
-// Launch: grid (ceil(((nx+1)/2) / 128), ny, nz), block 128.
+// Launch: grid (ceil(((nx+1)/2) / 128), ny, ceil(nz/2)), block 128.
 template <bool FIRST>
 __global__ void __launch_bounds__(128)
 sor_sweep_kernel(PDims d, int colour, float omega, float h2, float *__restrict__ ec, const float *__restrict__ eo,
                  const float *__restrict__ rc, double *__restrict__ p_hi)
 {
     const int slot = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y + 1, k = blockIdx.z + 1;
-    const int q = (colour + 1 + j + k) & 1;
-    const int i = 2 * slot + 1 + q;
-    if (i > d.nx) return;
-    const long long c = (long long)k * d.cplane + (long long)j * d.cpitch + 1 + slot;
-    float e_old = 0.0f;
-    if (FIRST) {
-        p_hi[pidx(d, i, j, k)] += (double)ec[c];
-    } else {
-        e_old = ec[c];
+    const int j = blockIdx.y + 1;
+    const int k0 = 2 * blockIdx.z + 1;
+    if (2 * slot + 1 > d.nx) return;  // no cell of either colour at this slot
+    const int jm = (j == 1) ? d.ny : j - 1;
+    const int jp = (j == d.ny) ? 1 : j + 1;
+    const bool need_nb = !FIRST || colour == 1;  // on the first red half-sweep every neighbour is still 0
+    float upd[2];
+    long long cc[2];
+    bool ok[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int k = k0 + h;
+        const int q = (colour + 1 + j + k) & 1;
+        const int i = 2 * slot + 1 + q;
+        ok[h] = i <= d.nx && k <= d.nz;
+        const long long c = (long long)k * d.cplane + (long long)j * d.cpitch + 1 + slot;
+        cc[h] = c;
+        upd[h] = 0.0f;
+        if (!ok[h]) continue;
+        float e_old = 0.0f;
+        if (FIRST) {
+            p_hi[pidx(d, i, j, k)] += (double)ec[c];
+        } else {
+            e_old = ec[c];
+        }
+        float s = 0.0f;
+        if (need_nb) {
+            const long long row = (long long)k * d.cplane;
+            s = (eo[c - 1 + q] + eo[c + q]) +
+                (eo[row + (long long)jm * d.cpitch + 1 + slot] + eo[row + (long long)jp * d.cpitch + 1 + slot]) +
+                (eo[c - d.cplane] + eo[c + d.cplane]);
+        }
+        upd[h] = e_old + omega * ((s - h2 * rc[c]) / pdiag(d, i, k) - e_old);
     }
-    float s = 0.0f;
-    if (!FIRST || colour == 1) {  // on the first red half-sweep every neighbour is still 0
-        const int jm = (j == 1) ? d.ny : j - 1;
-        const int jp = (j == d.ny) ? 1 : j + 1;
-        const long long row = (long long)k * d.cplane;
-        s = (eo[c - 1 + q] + eo[c + q]) +
-            (eo[row + (long long)jm * d.cpitch + 1 + slot] + eo[row + (long long)jp * d.cpitch + 1 + slot]) +
-            (eo[c - d.cplane] + eo[c + d.cplane]);
-    }
-    ec[c] = e_old + omega * ((s - h2 * rc[c]) / pdiag(d, i, k) - e_old);
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+        if (ok[h]) ec[cc[h]] = upd[h];
 }
 
 // r = b - A (p_hi + e) in FP64 (stored as FP32 in the colour arrays), with
@@ -108,6 +126,7 @@ poisson_resid_kernel(PDims d, const float *__restrict__ b, const double *__restr
 
 // Folds the partials (fixed order), updates the control block and sets the
 // while-node condition: continue while rho > tol and iters < max_iter.
+template <bool GRAPH>
 __global__ void __launch_bounds__(POI_RED_THREADS)
 poisson_test_kernel(const double *__restrict__ partials, int nblocks, PoissonCtl *ctl, double tol, int max_iter,
                     int m, int counting, cudaGraphConditionalHandle handle)
@@ -135,7 +154,7 @@ poisson_test_kernel(const double *__restrict__ partials, int nblocks, PoissonCtl
         if (bad) ctl->status = DEV_NONFINITE;
         const bool done = bad || bb < 1e-60 || rho <= tol || ctl->iters >= max_iter;
         ctl->done = done ? 1 : 0;
-        cudaGraphSetConditional(handle, done ? 0u : 1u);
+        if (GRAPH) cudaGraphSetConditional(handle, done ? 0u : 1u);
     }
 }
 
@@ -181,7 +200,7 @@ gbsw_status PoissonSolver::init(int nx, int ny, int nz, double dx, const float *
     d.nz = nz;
     d.pitch = (int)round_up((size_t)nx + 2, 32);
     d.plane = (long long)(ny + 2) * d.pitch;
-    d.cpitch = (int)round_up((size_t)(nx >> 1) + 2, 32);
+    d.cpitch = (int)round_up((size_t)(nx >> 1) + 2, 4);
     d.cplane = (long long)(ny + 2) * d.cpitch;
     d.dx = dx;
     b = b_dev;
@@ -244,7 +263,8 @@ gbsw_status PoissonSolver::build_graph()
     const size_t nc = (size_t)d.cplane * (size_t)(d.nz + 2);
     const float om = (float)omega, h2 = (float)(d.dx * d.dx);
     const int nxh = (d.nx + 1) / 2;
-    const dim3 sgrid(ceil_div(nxh, 128), d.ny, d.nz), sblock(128);
+    const dim3 sgrid(ceil_div(nxh, 128), d.ny, ceil_div(d.nz, 2)), sblock(128);
+    const dim3 fgrid(ceil_div(nxh, 128), d.ny, d.nz);
 
     cudaStream_t cs = nullptr;
     GBSW_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
@@ -266,7 +286,8 @@ gbsw_status PoissonSolver::build_graph()
         poisson_resid_kernel<<<POI_RED_BLOCKS, POI_RED_THREADS, 0, cs>>>(d, b, p_hi, e[0], e[1], r[0], r[1],
                                                                         partials);
         chk(cudaGetLastError());
-        poisson_test_kernel<<<1, POI_RED_THREADS, 0, cs>>>(partials, POI_RED_BLOCKS, ctl, tol, max_iter, m, 0, handle);
+        poisson_test_kernel<true><<<1, POI_RED_THREADS, 0, cs>>>(partials, POI_RED_BLOCKS, ctl, tol, max_iter, m, 0,
+                                                                  handle);
         chk(cudaGetLastError());
         // while node
         cudaStreamCaptureStatus cst;
@@ -281,8 +302,8 @@ gbsw_status PoissonSolver::build_graph()
         if (err == cudaSuccess) chk(cudaGraphAddNode(&cnode, cap_graph, deps, nullptr, ndeps, &cp));
         if (err == cudaSuccess) chk(cudaStreamUpdateCaptureDependencies(cs, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies));
         // epilogue: fold the last correction
-        poisson_fold_kernel<<<sgrid, sblock, 0, cs>>>(d, 0, p_hi, e[0]);
-        poisson_fold_kernel<<<sgrid, sblock, 0, cs>>>(d, 1, p_hi, e[1]);
+        poisson_fold_kernel<<<fgrid, sblock, 0, cs>>>(d, 0, p_hi, e[0]);
+        poisson_fold_kernel<<<fgrid, sblock, 0, cs>>>(d, 1, p_hi, e[1]);
         chk(cudaGetLastError());
     }
     cudaGraph_t captured = nullptr;
@@ -301,8 +322,8 @@ gbsw_status PoissonSolver::build_graph()
             }
             poisson_resid_kernel<<<POI_RED_BLOCKS, POI_RED_THREADS, 0, cs>>>(d, b, p_hi, e[0], e[1], r[0], r[1],
                                                                             partials);
-            poisson_test_kernel<<<1, POI_RED_THREADS, 0, cs>>>(partials, POI_RED_BLOCKS, ctl, tol, max_iter, m, 1,
-                                                              handle);
+            poisson_test_kernel<true><<<1, POI_RED_THREADS, 0, cs>>>(partials, POI_RED_BLOCKS, ctl, tol, max_iter, m,
+                                                                    1, handle);
             chk(cudaGetLastError());
         }
         cudaGraph_t body_out = nullptr;
@@ -328,6 +349,37 @@ gbsw_status PoissonSolver::enqueue()
     return GBSW_OK;
 }
 
+gbsw_status PoissonSolver::enqueue_fixed(int niter)
+{
+    if (niter < 0) return GBSW_ERR_ARG;
+    const size_t nc = (size_t)d.cplane * (size_t)(d.nz + 2);
+    const float om = (float)omega, h2 = (float)(d.dx * d.dx);
+    const dim3 sgrid(ceil_div((d.nx + 1) / 2, 128), d.ny, ceil_div(d.nz, 2)), sblock(128);
+    const dim3 fgrid(ceil_div((d.nx + 1) / 2, 128), d.ny, d.nz);
+    GBSW_CUDA_TRY(cudaMemsetAsync(e[0], 0, nc * sizeof(float), stream));
+    GBSW_CUDA_TRY(cudaMemsetAsync(e[1], 0, nc * sizeof(float), stream));
+    poisson_resid_kernel<<<POI_RED_BLOCKS, POI_RED_THREADS, 0, stream>>>(d, b, p_hi, e[0], e[1], r[0], r[1],
+                                                                        partials);
+    poisson_test_kernel<false><<<1, POI_RED_THREADS, 0, stream>>>(partials, POI_RED_BLOCKS, ctl, 0.0, niter, 0, 0, 0);
+    for (int it = 0; it < niter; ++it) {
+        if (it == 0) {
+            sor_sweep_kernel<true><<<sgrid, sblock, 0, stream>>>(d, 0, om, h2, e[0], e[1], r[0], p_hi);
+            sor_sweep_kernel<true><<<sgrid, sblock, 0, stream>>>(d, 1, om, h2, e[1], e[0], r[1], p_hi);
+        } else {
+            sor_sweep_kernel<false><<<sgrid, sblock, 0, stream>>>(d, 0, om, h2, e[0], e[1], r[0], p_hi);
+            sor_sweep_kernel<false><<<sgrid, sblock, 0, stream>>>(d, 1, om, h2, e[1], e[0], r[1], p_hi);
+        }
+    }
+    poisson_resid_kernel<<<POI_RED_BLOCKS, POI_RED_THREADS, 0, stream>>>(d, b, p_hi, e[0], e[1], r[0], r[1],
+                                                                        partials);
+    poisson_test_kernel<false><<<1, POI_RED_THREADS, 0, stream>>>(partials, POI_RED_BLOCKS, ctl, 0.0, niter, niter,
+                                                                   1, 0);
+    poisson_fold_kernel<<<fgrid, sblock, 0, stream>>>(d, 0, p_hi, e[0]);
+    poisson_fold_kernel<<<fgrid, sblock, 0, stream>>>(d, 1, p_hi, e[1]);
+    GBSW_LAUNCH_CHECK();
+    return GBSW_OK;
+}
+
 gbsw_status PoissonSolver::record(PoissonCtl *dst)
 {
     GBSW_CUDA_TRY(cudaMemcpyAsync(dst, ctl, sizeof(PoissonCtl), cudaMemcpyDeviceToDevice, stream));
@@ -344,6 +396,7 @@ extern "C" gbsw_status poisson_solve(int nx, int ny, int nz, double dx, float *p
 {
     if (nx < 2 || ny < 2 || nz < 2 || (ny & 1) || nx > 8192 || ny > 8192 || nz > 8192 || !(dx > 0) || !p || !b)
         return GBSW_ERR_ARG;
+    const bool fixed = tol < 0.0;  // paper mode: exactly max_iter iterations, no convergence test
     cudaStream_t s = (cudaStream_t)stream;
     PoissonSolver S;
     float *bp = nullptr;
@@ -366,7 +419,7 @@ extern "C" gbsw_status poisson_solve(int nx, int ny, int nz, double dx, float *p
         }
         st = S.init(nx, ny, nz, dx, bp, s);
         if (st != GBSW_OK) break;
-        st = S.configure(omega, tol, max_iter, check_every);
+        st = S.configure(omega, fixed ? 0.0 : tol, max_iter, check_every);
         if (st != GBSW_OK) break;
         const dim3 g(ceil_div(nx, 128), ny, nz), blk(128);
         poisson_scatter_kernel<<<g, blk, 0, s>>>(S.d, b, bp, nullptr);
@@ -376,7 +429,7 @@ extern "C" gbsw_status poisson_solve(int nx, int ny, int nz, double dx, float *p
             st = GBSW_ERR_CUDA;
             break;
         }
-        st = S.enqueue();
+        st = fixed ? S.enqueue_fixed(max_iter) : S.enqueue();
         if (st != GBSW_OK) break;
         poisson_gather_kernel<<<g, blk, 0, s>>>(S.d, S.p_hi, p);
         if ((e = cudaGetLastError()) != cudaSuccess ||
@@ -393,5 +446,6 @@ extern "C" gbsw_status poisson_solve(int nx, int ny, int nz, double dx, float *p
     if (iters) *iters = host.iters;
     if (rel_res) *rel_res = host.rho;
     if (host.status != DEV_OK) return dev_status_to_gbsw(host.status);
+    if (fixed) return GBSW_OK;
     return host.done && (host.rho <= tol || host.bb < 1e-60) ? GBSW_OK : GBSW_NOT_CONVERGED;
 }

@@ -58,6 +58,10 @@ public:
     gbsw_status configure(double omega, double tol, int max_iter, int check_every);
     // Enqueue one solve (asynchronous; one graph launch).
     gbsw_status enqueue();
+    // Enqueue exactly niter iterations with no convergence test (the
+    // paper's fixed-count SOR), launched directly on the stream; the control
+    // block receives the final residual.
+    gbsw_status enqueue_fixed(int niter);
     // Copy the control block of the last solve into *out (device -> device).
     gbsw_status record(PoissonCtl *dev_dst);
 

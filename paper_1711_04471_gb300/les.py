@@ -72,6 +72,10 @@ class LES:
         p.check_every = p.check_every if check_every is None else int(check_every)
         N.check(N.lib().les_set_solver(self._h, p.omega, p.tol, p.max_iter, p.check_every), "les_set_solver")
 
+    def set_fixed_iterations(self, niter: int):
+        """Paper mode: exactly niter SOR iterations per step (0 = tolerance-driven)."""
+        N.check(N.lib().les_set_fixed_iterations(self._h, int(niter)), "les_set_fixed_iterations")
+
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             N.lib().les_destroy(self._h)
