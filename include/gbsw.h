@@ -124,6 +124,52 @@ gbsw_status sw_set_blocking(gbsw_sw *sw, int steps_per_launch);
 void sw_destroy(gbsw_sw *sw);
 
 /* ------------------------------------------------------------------------
+ * Batched 2DSW ensemble: n independent instances (each its own size,
+ * bathymetry and initial state) of the 2DSW step above, advanced together.
+ * The paper has no ensemble; this is the step of Sec. 6.2 applied to many
+ * grids at once.  One sw_batch_step call is one CUDA-graph launch of a
+ * persistent cooperative kernel that processes every instance's tiles
+ * level after level (a level = steps_per_level fused time steps), with a
+ * bounded grid barrier between levels.
+ * ---------------------------------------------------------------------- */
+
+typedef struct gbsw_sw_batch gbsw_sw_batch;
+
+/* params, H[m], eta0[m]: n entries, each as in sw_create (host, FP64,
+ * ny*nx).  Synchronous. */
+gbsw_status sw_batch_create(int n, const gbsw_sw_params *params, const double *const *H,
+                            const double *const *eta0, void *stream, gbsw_sw_batch **out);
+
+/* Advance every instance by nsteps (asynchronous; one graph launch, cached
+ * per nsteps). */
+gbsw_status sw_batch_step(gbsw_sw_batch *b, int nsteps);
+
+/* The same steps issued as one launch per instance and fused level (the
+ * unbatched baseline the persistent kernel is measured against). */
+gbsw_status sw_batch_step_separate(gbsw_sw_batch *b, int nsteps);
+
+/* FP64 volumes (and wet volumes) of every instance into host arrays of n
+ * (either may be NULL); synchronises; reports GBSW_ERR_TIMEOUT if a grid
+ * barrier wait gave up, GBSW_ERR_NONFINITE on NaN/Inf. */
+gbsw_status sw_batch_volumes(gbsw_sw_batch *b, double *volumes, double *wet_volumes);
+
+/* Copy instance m's state to host buffers in the layout of sw_get_state. */
+gbsw_status sw_batch_get_state(gbsw_sw_batch *b, int m, float *eta, float *u, float *v);
+
+/* Tiling: fused steps per level (1..4) and rows per work item (8..65536). */
+gbsw_status sw_batch_set_tiling(gbsw_sw_batch *b, int steps_per_level, int rows_per_item);
+gbsw_status sw_batch_get_tiling(gbsw_sw_batch *b, int *steps_per_level, int *rows_per_item);
+
+/* Time every (steps_per_level, rows_per_item) candidate on this batch
+ * (state saved and restored), keep the fastest and return it.  If
+ * cache_path is not NULL the choice is looked up in / appended to that
+ * text file, keyed by device name and instance sizes. */
+gbsw_status sw_batch_autotune(gbsw_sw_batch *b, int trial_steps, const char *cache_path, int *steps_per_level,
+                              int *rows_per_item);
+
+void sw_batch_destroy(gbsw_sw_batch *b);
+
+/* ------------------------------------------------------------------------
  * Urban LES (Sec. 6.3.1: each step runs velnw, bondv1, velfg, feedbf, les,
  * adam and press, in that order).
  *

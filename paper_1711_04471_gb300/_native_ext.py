@@ -28,5 +28,15 @@ def declare(L, sig):
     sig(L, "les_set_solver", C.c_int, [vp, C.c_double, C.c_double, C.c_int, C.c_int])
     sig(L, "les_set_fixed_iterations", C.c_int, [vp, C.c_int])
     sig(L, "les_destroy", None, [vp])
+    sp = C.POINTER(C.c_double)
+    sig(L, "sw_batch_create", C.c_int, [C.c_int, vp, C.POINTER(sp), C.POINTER(sp), vp, C.POINTER(vp)])
+    sig(L, "sw_batch_step", C.c_int, [vp, C.c_int])
+    sig(L, "sw_batch_step_separate", C.c_int, [vp, C.c_int])
+    sig(L, "sw_batch_volumes", C.c_int, [vp, dp, dp])
+    sig(L, "sw_batch_get_state", C.c_int, [vp, C.c_int, vp, vp, vp])
+    sig(L, "sw_batch_set_tiling", C.c_int, [vp, C.c_int, C.c_int])
+    sig(L, "sw_batch_get_tiling", C.c_int, [vp, ip, ip])
+    sig(L, "sw_batch_autotune", C.c_int, [vp, C.c_int, C.c_char_p, ip, ip])
+    sig(L, "sw_batch_destroy", None, [vp])
     sig(L, "poisson_solve", C.c_int, [C.c_int, C.c_int, C.c_int, C.c_double, vp, vp, C.c_double, C.c_double,
                                       C.c_int, C.c_int, vp, ip, dp])

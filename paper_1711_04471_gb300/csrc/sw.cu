@@ -17,6 +17,71 @@
 
 using namespace gbsw;
 
+namespace gbsw {
+
+// FP64 volume partial sums over rows blockIdx.x, blockIdx.x + gridDim.x, ...
+// partials[3*b + {0,1,2}] = sum h, sum of h over wet cells, count of
+// non-finite eta.  The order of every sum depends only on (nx, ny).
+__global__ void __launch_bounds__(SW_VOL_THREADS)
+sw_volume_partial_kernel(SWDev p, const float *__restrict__ H, const float *__restrict__ eta,
+                         double *__restrict__ partials)
+{
+    __shared__ double red[SW_VOL_THREADS / 32];
+    double s = 0.0, sw = 0.0, bad = 0.0;
+    for (int j = blockIdx.x; j < p.ny; j += gridDim.x) {
+        const size_t row = (size_t)j * p.pitch;
+        for (int i = threadIdx.x; i < p.nx; i += blockDim.x) {
+            const float e = eta[row + i], hh = H[row + i];
+            if (!isfinite(e)) bad += 1.0;
+            const double h = (double)hh + (double)e;
+            s += h;
+            if (hh + e > p.hmin) sw += h;
+        }
+    }
+    s = block_sum_f64<SW_VOL_THREADS / 32>(s, red);
+    sw = block_sum_f64<SW_VOL_THREADS / 32>(sw, red);
+    bad = block_sum_f64<SW_VOL_THREADS / 32>(bad, red);
+    if (threadIdx.x == 0) {
+        partials[3 * blockIdx.x + 0] = s;
+        partials[3 * blockIdx.x + 1] = sw;
+        partials[3 * blockIdx.x + 2] = bad;
+    }
+}
+
+// Second pass: one block folds the partials in a fixed order and scales.
+__global__ void __launch_bounds__(SW_VOL_THREADS)
+sw_volume_final_kernel(const double *__restrict__ partials, int nblocks, double area, double *__restrict__ out)
+{
+    __shared__ double red[SW_VOL_THREADS / 32];
+    double s = 0.0, sw = 0.0, bad = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+        s += partials[3 * b + 0];
+        sw += partials[3 * b + 1];
+        bad += partials[3 * b + 2];
+    }
+    s = block_sum_f64<SW_VOL_THREADS / 32>(s, red);
+    sw = block_sum_f64<SW_VOL_THREADS / 32>(sw, red);
+    bad = block_sum_f64<SW_VOL_THREADS / 32>(bad, red);
+    if (threadIdx.x == 0) {
+        out[0] = s * area;
+        out[1] = sw * area;
+        out[2] = bad;
+    }
+}
+
+// Wet mask as bytes (packed nx per row) for host read-back.
+__global__ void sw_wet_mask_kernel(SWDev p, const float *__restrict__ H, const float *__restrict__ eta,
+                                   uint8_t *__restrict__ wet)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= p.nx || j >= p.ny) return;
+    const size_t g = (size_t)j * p.pitch + i;
+    wet[(size_t)j * p.nx + i] = H[g] + eta[g] > p.hmin;
+}
+
+}  // namespace gbsw
+
 struct gbsw_sw {
     gbsw_sw_params p;
     SWDev d;

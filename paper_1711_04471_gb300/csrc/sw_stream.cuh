@@ -58,24 +58,37 @@ struct SWStageLines {
     float es[2][SWS_LINE];
 };
 
-template <int T>
-__global__ void __launch_bounds__(SWS_THREADS)
-sw_stream_kernel(SWDev p, int rows_per_cta, const float *__restrict__ H, const float *__restrict__ eta_in,
-                 const float *__restrict__ u_in, const float *__restrict__ v_in, float *__restrict__ eta_out,
-                 float *__restrict__ u_out, float *__restrict__ v_out)
+// Loads of the level-0 rows: through the read-only path when the inputs
+// cannot change during the kernel (one fused launch), through L2 only
+// (coherent across SMs) inside the persistent ensemble kernel, where other
+// CTAs rewrite the buffers between levels.
+enum class SWLoad { ReadOnly, L2 };
+
+template <SWLoad LP>
+__device__ __forceinline__ float sw_load(const float *ptr)
+{
+    if constexpr (LP == SWLoad::ReadOnly) return __ldg(ptr);
+    else return __ldcg(ptr);
+}
+
+// One (strip, row segment) work item: T fused steps of the columns of
+// strip `strip` (SWS_THREADS wide, W = SWS_THREADS - 4T written) for output
+// rows [r0, r1).  All threads of the CTA must call it together.
+template <int T, SWLoad LP>
+__device__ __forceinline__ void sw_stream_tile(const SWDev &p, int strip, int r0, int r1,
+                                               const float *__restrict__ H, const float *__restrict__ eta_in,
+                                               const float *__restrict__ u_in, const float *__restrict__ v_in,
+                                               float *__restrict__ eta_out, float *__restrict__ u_out,
+                                               float *__restrict__ v_out, SWStageLines *lines)
 {
     constexpr int W = SWS_THREADS - 4 * T;
-    __shared__ SWStageLines lines[T];
-
     const int x = threadIdx.x;
     const int c = x + SWS_PAD;                      // index in a line buffer
-    const int gi = blockIdx.x * W - 2 * T + x;      // grid column of this thread
+    const int gi = strip * W - 2 * T + x;           // grid column of this thread
     const bool col_in = gi >= 0 && gi < p.nx;
     const bool owned = x >= 2 * T && x < 2 * T + W && col_in;
     const bool u_open = gi >= 0 && gi < p.nx - 1;   // not a wall face
-    const int r0 = blockIdx.y * rows_per_cta;
-    const int r1 = min(p.ny, r0 + rows_per_cta);
-    if (r0 >= p.ny) return;
+    __syncthreads();  // the line buffers may still be in use by the previous work item
 
     // zero the guard columns once (they only feed discarded halo columns)
     if (x < 2 * T) {
@@ -102,10 +115,10 @@ sw_stream_kernel(SWDev p, int rows_per_cta, const float *__restrict__ H, const f
         SWRow r{0.0f, 0.0f, 0.0f, 0.0f};
         if (col_in && n >= 0 && n < p.ny) {
             const size_t g = (size_t)n * p.pitch + gi;
-            r.eta = __ldg(eta_in + g);
-            r.u = __ldg(u_in + g);
-            r.v = __ldg(v_in + g);
-            r.H = __ldg(H + g);
+            r.eta = sw_load<LP>(eta_in + g);
+            r.u = sw_load<LP>(u_in + g);
+            r.v = sw_load<LP>(v_in + g);
+            r.H = sw_load<LP>(H + g);
         }
         return r;
     };
@@ -132,7 +145,7 @@ sw_stream_kernel(SWDev p, int rows_per_cta, const float *__restrict__ H, const f
 #pragma unroll
         for (int t = 0; t < T; ++t) {
             const int s0 = (P - 3 * t) & 3;  // slot of row m = n - 3t
-            hn[t] = in[t].H + in[t].eta;
+            hn[t] = __fadd_rn(in[t].H, in[t].eta);
             lines[t].eta[s0 & 1][c] = in[t].eta;
             lines[t].h[s0][c] = hn[t];
         }
@@ -148,12 +161,12 @@ sw_stream_kernel(SWDev p, int rows_per_cta, const float *__restrict__ H, const f
             if (u_open) {
                 const float ee = lines[t].eta[s0 & 1][c + 1];
                 const bool we = lines[t].h[s0][c + 1] > hmin;
-                uv = sw_face_mask(in[t].u - p.gdt_dx * (ee - in[t].eta), wc, we);
+                uv = sw_face_mask(sw_predict(in[t].u, p.gdt_dx, ee, in[t].eta), wc, we);
             }
             un[t] = uv;
             float vv = 0.0f;
             if (m - 1 >= 0 && m - 1 < p.ny - 1)
-                vv = sw_face_mask(R[t].v1 - p.gdt_dy * (in[t].eta - R[t].eta1), R[t].h1 > hmin, wc);
+                vv = sw_face_mask(sw_predict(R[t].v1, p.gdt_dy, in[t].eta, R[t].eta1), R[t].h1 > hmin, wc);
             vn1[t] = vv;
             lines[t].up[s0 & 1][c] = uv;
         }
@@ -170,7 +183,7 @@ sw_stream_kernel(SWDev p, int rows_per_cta, const float *__restrict__ H, const f
             const float fw = sw_upwind(uw, hw, h1);
             const float gn = sw_upwind(vn1[t], h1, hn[t]);
             const float gs = sw_upwind(R[t].vp2, R[t].h2, h1);
-            es1[t] = R[t].eta1 - (p.dt_dx * (fe - fw) + p.dt_dy * (gn - gs));
+            es1[t] = __fsub_rn(R[t].eta1, __fmaf_rn(p.dt_dx, __fsub_rn(fe, fw), __fmul_rn(p.dt_dy, __fsub_rn(gn, gs))));
             lines[t].es[s1 & 1][c] = es1[t];
         }
         __syncthreads();
@@ -187,9 +200,10 @@ sw_stream_kernel(SWDev p, int rows_per_cta, const float *__restrict__ H, const f
                 const float ws = R[t].h3 > hmin ? 1.0f : 0.0f;
                 const float ee = lines[t].es[s2 & 1][c + 1];
                 const float ew = lines[t].es[s2 & 1][c - 1];
-                const float cnt = (we + ww) + (wn + ws);
-                const float sum = (we * ee + ww * ew) + (wn * es1[t] + ws * R[t].es3);
-                out = (1.0f - p.q * cnt) * es2 + p.q * sum;
+                const float cnt = (we + ww) + (wn + ws);  // small integers: exact
+                const float sum = __fadd_rn(__fadd_rn(__fmul_rn(we, ee), __fmul_rn(ww, ew)),
+                                            __fadd_rn(__fmul_rn(wn, es1[t]), __fmul_rn(ws, R[t].es3)));
+                out = __fmaf_rn(p.q, sum, __fmul_rn(__fsub_rn(1.0f, __fmul_rn(p.q, cnt)), es2));
             }
             mail[t] = SWRow{out, R[t].up2, R[t].vp2, R[t].H2};
             // roll the window
@@ -225,6 +239,21 @@ sw_stream_kernel(SWDev p, int rows_per_cta, const float *__restrict__ H, const f
         iteration(std::integral_constant<int, 2>{}, n4);
         iteration(std::integral_constant<int, 3>{}, n4);
     }
+}
+
+// One fused launch of depth T over a single grid.  grid (strips, segments),
+// block SWS_THREADS; rows_per_cta rows per segment.
+template <int T>
+__global__ void __launch_bounds__(SWS_THREADS)
+sw_stream_kernel(SWDev p, int rows_per_cta, const float *__restrict__ H, const float *__restrict__ eta_in,
+                 const float *__restrict__ u_in, const float *__restrict__ v_in, float *__restrict__ eta_out,
+                 float *__restrict__ u_out, float *__restrict__ v_out)
+{
+    __shared__ SWStageLines lines[T];
+    const int r0 = blockIdx.y * rows_per_cta;
+    if (r0 >= p.ny) return;
+    const int r1 = min(p.ny, r0 + rows_per_cta);
+    sw_stream_tile<T, SWLoad::ReadOnly>(p, blockIdx.x, r0, r1, H, eta_in, u_in, v_in, eta_out, u_out, v_out, lines);
 }
 
 }  // namespace gbsw

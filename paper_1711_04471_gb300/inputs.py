@@ -129,7 +129,8 @@ def _eval_modes(wl, ang, phi, xs, ys):
 
 def sw_wetdry(n: int = 4096, seed: int = 1001, dx: float = 10.0, dt: float = 0.1,
               mean_depth: float = 50.0, hill_amp: float = 60.0, n_hills: int = 32,
-              surf_amp: float = 0.5, dry_target: float = 0.15, hmin: float = 0.05) -> SWInput:
+              surf_amp: float = 0.5, dry_target: float = 0.15, hmin: float = 0.05,
+              sample: int = 512, bisect_iters: int = 40) -> SWInput:
     """Random bathymetry with ~15 % dry land and a random-phase surface perturbation.
 
     H = mean_depth - sum_k hill_amp * exp(-|x - c_k|^2 / (2 sigma_k^2)), with
@@ -143,7 +144,7 @@ def sw_wetdry(n: int = 4096, seed: int = 1001, dx: float = 10.0, dt: float = 0.1
     sfac = rng.uniform(n_hills, 0.5, 1.5)
     wl, ang, phi = _surface_modes(n, n, rng, lmin=min(64.0, n / 4), lmax=min(512.0, n))
 
-    stride = max(1, n // 512)
+    stride = max(1, n // sample)
     xs = np.arange(0, n, stride, dtype=np.float64) + 0.5
     modes_s = _eval_modes(wl, ang, phi, xs, xs)
     eta_s = surf_amp * modes_s / np.abs(modes_s).max()
@@ -153,7 +154,7 @@ def sw_wetdry(n: int = 4096, seed: int = 1001, dx: float = 10.0, dt: float = 0.1
         return float(np.mean(Hs + eta_ <= hmin))
 
     lo, hi = 1.0, float(n)
-    for _ in range(40):
+    for _ in range(bisect_iters):
         mid = 0.5 * (lo + hi)
         if dry_frac(mid, xs, eta_s) < dry_target:
             lo = mid
@@ -178,7 +179,7 @@ def sw_ensemble_sizes(count: int = 512, seed: int = 1002, nmin: int = 64, nmax: 
 
 def sw_ensemble_member(n: int, seed: int, idx: int, dx: float = 10.0, dt: float = 0.1) -> SWInput:
     """One ensemble instance: its own wet/dry bathymetry plus the 1 m, 5-cell hump."""
-    base = sw_wetdry(n, derive_seed(seed, idx), dx=dx, dt=dt)
+    base = sw_wetdry(n, derive_seed(seed, idx), dx=dx, dt=dt, sample=64, bisect_iters=24)
     xc = np.arange(n, dtype=np.float64) + 0.5
     r2 = (xc[None, :] - n / 2) ** 2 + (xc[:, None] - n / 2) ** 2
     hump = np.exp(-r2 / (2.0 * 25.0))

@@ -75,3 +75,79 @@ class SW:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class SWBatch:
+    """Ensemble of independent 2DSW instances stepped by one persistent
+    kernel (sw_batch_* entry points)."""
+
+    def __init__(self, members, stream=None):
+        L = N.lib()
+        self.n = len(members)
+        self.shapes = [(m.ny, m.nx) for m in members]
+        params = (N.SWParams * self.n)()
+        self._H = [np.ascontiguousarray(m.H, dtype=np.float64) for m in members]
+        self._E = [np.ascontiguousarray(m.eta0, dtype=np.float64) for m in members]
+        for k, m in enumerate(members):
+            params[k] = N.SWParams(m.nx, m.ny, m.dx, m.dy, m.dt, m.g, m.eps, m.hmin)
+        dpp = C.POINTER(C.c_double)
+        Hp = (dpp * self.n)(*[a.ctypes.data_as(dpp) for a in self._H])
+        Ep = (dpp * self.n)(*[a.ctypes.data_as(dpp) for a in self._E])
+        h = C.c_void_p()
+        N.check(L.sw_batch_create(self.n, C.cast(params, C.c_void_p), Hp, Ep, N.stream_handle(stream), C.byref(h)),
+                "sw_batch_create")
+        self._h = h
+        self._H = self._E = None
+
+    def step(self, nsteps: int):
+        N.check(N.lib().sw_batch_step(self._h, int(nsteps)), "sw_batch_step")
+
+    def step_separate(self, nsteps: int):
+        N.check(N.lib().sw_batch_step_separate(self._h, int(nsteps)), "sw_batch_step_separate")
+
+    def volumes(self):
+        v = np.empty(self.n)
+        w = np.empty(self.n)
+        N.check(N.lib().sw_batch_volumes(self._h, N.ptr(v, C.c_double), N.ptr(w, C.c_double)), "sw_batch_volumes")
+        return v, w
+
+    def get_state(self, m: int):
+        ny, nx = self.shapes[m]
+        eta = np.empty((ny, nx), np.float32)
+        u = np.empty((ny, nx + 1), np.float32)
+        v = np.empty((ny + 1, nx), np.float32)
+        N.check(N.lib().sw_batch_get_state(self._h, int(m), eta.ctypes.data_as(C.c_void_p),
+                                           u.ctypes.data_as(C.c_void_p), v.ctypes.data_as(C.c_void_p)),
+                "sw_batch_get_state")
+        return dict(eta=eta, u=u, v=v)
+
+    def set_tiling(self, steps_per_level: int, rows_per_item: int):
+        N.check(N.lib().sw_batch_set_tiling(self._h, int(steps_per_level), int(rows_per_item)), "sw_batch_set_tiling")
+
+    def get_tiling(self):
+        t, r = C.c_int(), C.c_int()
+        N.check(N.lib().sw_batch_get_tiling(self._h, C.byref(t), C.byref(r)), "sw_batch_get_tiling")
+        return t.value, r.value
+
+    def autotune(self, trial_steps: int = 12, cache_path: str | None = None):
+        t, r = C.c_int(), C.c_int()
+        cp = None if cache_path is None else cache_path.encode()
+        N.check(N.lib().sw_batch_autotune(self._h, int(trial_steps), cp, C.byref(t), C.byref(r)), "sw_batch_autotune")
+        return t.value, r.value
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            N.lib().sw_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
