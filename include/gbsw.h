@@ -282,6 +282,29 @@ void les_destroy(gbsw_les *les);
 gbsw_status poisson_solve(int nx, int ny, int nz, double dx, float *p, const float *b, double omega, double tol,
                           int max_iter, int check_every, void *stream, int *iters, double *rel_res);
 
+/* ------------------------------------------------------------------------
+ * Learned warm start for the pressure solve: a 3-D convolutional U-Net
+ * (not in the paper; SOR from Sec. 6.3.1 still decides the answer).  The
+ * 3x3x3 convolutions run on the tensor cores (tcgen05, BF16 operands, FP32
+ * accumulation in tensor memory).
+ * ---------------------------------------------------------------------- */
+
+/*
+ * One 3x3x3 convolution with zero padding (operator-level entry point).
+ *   x     device, nsamples*D*H*W*cin FP32, channels last (rounded to BF16)
+ *   w     device, 27*cout*cin FP32, w[tap][co][ci] with tap = (dz+1)*9 +
+ *         (dy+1)*3 + (dx+1) for input offsets dz, dy, dx (rounded to BF16)
+ *   bias  device, cout FP32 (epilogue 0 only)
+ *   epilogue 0: y = max(conv + bias, 0); 1: y = conv; 2: y = conv where
+ *         mask > 0, else 0 (mask: device FP32, same shape as y)
+ *   y     device, nsamples*D*H*W*cout FP32 (the FP32 accumulator, unrounded)
+ * cin, cout in {16, 32, 64} (pairs used by the network); W a power of two
+ * of at least 16 or a multiple of 128; H a multiple of 128/min(W, 128).
+ * Synchronous; allocates a temporary BF16 copy of x and the packed weights.
+ */
+gbsw_status unet_conv3d(int nsamples, int D, int H, int W, int cin, int cout, const float *x, const float *w,
+                        const float *bias, int epilogue, const float *mask, float *y, void *stream);
+
 /*
  * Volume reduction that allocates no memory.  The paper has no
  * counterpart: this entry point exists for callers that cannot call
