@@ -220,6 +220,7 @@ typedef struct {
     double rel_res;         /* final ||b - A p|| / ||b|| */
     float ms_predictor;     /* device time of velnw .. rhs */
     float ms_solve;         /* device time of the pressure solve */
+    float ms_guess;         /* device time of the learned warm start (0 without) */
 } gbsw_les_stats;
 
 /* Field ids for les_get_field / les_set_field.  Every field is exchanged
@@ -304,6 +305,50 @@ gbsw_status poisson_solve(int nx, int ny, int nz, double dx, float *p, const flo
  */
 gbsw_status unet_conv3d(int nsamples, int D, int H, int W, int cin, int cout, const float *x, const float *w,
                         const float *bias, int epilogue, const float *mask, float *y, void *stream);
+
+typedef struct gbsw_unet gbsw_unet;
+
+/* Number of FP32 parameters: for each 3x3x3 layer l1a (2->16), l1b (16->16),
+ * l2a (16->32), l2b (32->32), l3a (32->64), l3b (64->32), l2c (64->16),
+ * l1c (32->16) the weights w[27][cout][cin] then the bias[cout], followed
+ * by the 1x1 head's 16 weights and its bias. */
+int unet_num_params(void);
+
+/* Create the network with He-normal weights drawn from `seed`. */
+gbsw_status unet_create(unsigned long long seed, void *stream, gbsw_unet **out);
+
+/* Copy all n = unet_num_params() parameters to / from host memory. */
+gbsw_status unet_get_params(gbsw_unet *net, float *host, int n);
+gbsw_status unet_set_params(gbsw_unet *net, const float *host, int n);
+
+/*
+ * Forward pass.  x: device, n*D*H*W*2 FP32 (channels last: the scaled
+ * right-hand side and previous pressure); y: device, n*D*H*W FP32 (the
+ * scaled pressure increment).  D, H, W multiples of 4, W/4 a power of two
+ * >= 16 (or a multiple of 128).  Synchronous.
+ */
+gbsw_status unet_forward(gbsw_unet *net, int n, int D, int H, int W, const float *x, float *y);
+
+/* MSE loss against target (device, n*D*H*W FP32) and the parameter
+ * gradients (host array of unet_num_params(), or NULL), no update. */
+gbsw_status unet_gradients(gbsw_unet *net, int n, int D, int H, int W, const float *x, const float *target,
+                           float *grads_host, double *loss);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on the MSE loss; *loss
+ * (host, may be NULL) receives the loss before the update. */
+gbsw_status unet_train_step(gbsw_unet *net, int n, int D, int H, int W, const float *x, const float *target,
+                            float lr, double *loss);
+
+void unet_destroy(gbsw_unet *net);
+
+/*
+ * Learned warm start for les_step: before each pressure solve the network
+ * maps [b dx^2 / s, p_prev / s] (s = dx^2 rms(b)) to an increment that is
+ * added to the previous pressure; SOR then runs to the same tolerance.
+ * net = NULL restores the plain warm start (previous pressure).  The
+ * context does not own the network; keep it alive while it is set.
+ */
+gbsw_status les_set_warm_start(gbsw_les *les, gbsw_unet *net);
 
 /*
  * Volume reduction that allocates no memory.  The paper has no

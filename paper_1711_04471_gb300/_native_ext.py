@@ -12,7 +12,7 @@ class LESParams(C.Structure):
 
 class LESStats(C.Structure):
     _fields_ = [("iters", C.c_int), ("status", C.c_int), ("rel_res", C.c_double), ("ms_predictor", C.c_float),
-                ("ms_solve", C.c_float)]
+                ("ms_solve", C.c_float), ("ms_guess", C.c_float)]
 
 
 def declare(L, sig):
@@ -38,5 +38,15 @@ def declare(L, sig):
     sig(L, "sw_batch_get_tiling", C.c_int, [vp, ip, ip])
     sig(L, "sw_batch_autotune", C.c_int, [vp, C.c_int, C.c_char_p, ip, ip])
     sig(L, "sw_batch_destroy", None, [vp])
+    sig(L, "unet_conv3d", C.c_int, [C.c_int] * 6 + [vp, vp, vp, C.c_int, vp, vp, vp])
+    sig(L, "unet_num_params", C.c_int, [])
+    sig(L, "unet_create", C.c_int, [C.c_ulonglong, vp, C.POINTER(vp)])
+    sig(L, "unet_get_params", C.c_int, [vp, vp, C.c_int])
+    sig(L, "unet_set_params", C.c_int, [vp, vp, C.c_int])
+    sig(L, "unet_forward", C.c_int, [vp, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp])
+    sig(L, "unet_gradients", C.c_int, [vp, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp, dp])
+    sig(L, "unet_train_step", C.c_int, [vp, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, C.c_float, dp])
+    sig(L, "unet_destroy", None, [vp])
+    sig(L, "les_set_warm_start", C.c_int, [vp, vp])
     sig(L, "poisson_solve", C.c_int, [C.c_int, C.c_int, C.c_int, C.c_double, vp, vp, C.c_double, C.c_double,
                                       C.c_int, C.c_int, vp, ip, dp])

@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "poisson.cuh"
+#include "unet_ops.cuh"
 
 using namespace gbsw;
 
@@ -291,6 +292,7 @@ struct gbsw_les {
     int ctl_log_len;
     int step;
     int fixed_iters;       // > 0: paper mode, exactly this many SOR iterations per step
+    gbsw_unet *net;        // learned warm start (not owned), NULL = previous pressure
     size_t n;              // elements per padded field
 };
 
@@ -459,17 +461,28 @@ gbsw_status les_step(gbsw_les *s, int nsteps, gbsw_les_stats *stats)
     if (st != GBSW_OK) return st;
     std::vector<cudaEvent_t> ev;
     if (stats) {
-        ev.resize(3 * (size_t)nsteps);
+        ev.resize(4 * (size_t)nsteps);
         for (auto &x : ev) GBSW_CUDA_TRY(cudaEventCreate(&x));
     }
+    PadDims pd;
+    pd.nx = s->q.d.nx;
+    pd.ny = s->q.d.ny;
+    pd.nz = s->q.d.nz;
+    pd.pitch = s->q.d.pitch;
+    pd.plane = s->q.d.plane;
     for (int t = 0; t < nsteps && st == GBSW_OK; ++t) {
-        if (stats) cudaEventRecord(ev[3 * t], s->stream);
+        if (stats) cudaEventRecord(ev[4 * t], s->stream);
         st = les_predictor(s);
         if (st != GBSW_OK) break;
-        if (stats) cudaEventRecord(ev[3 * t + 1], s->stream);
+        if (stats) cudaEventRecord(ev[4 * t + 1], s->stream);
+        if (s->net) {
+            st = unet_warm_start(s->net, s->b, s->solver.p_hi, pd, s->p.dx, s->stream);
+            if (st != GBSW_OK) break;
+        }
+        if (stats) cudaEventRecord(ev[4 * t + 2], s->stream);
         st = s->fixed_iters > 0 ? s->solver.enqueue_fixed(s->fixed_iters) : s->solver.enqueue();
         if (st != GBSW_OK) break;
-        if (stats) cudaEventRecord(ev[3 * t + 2], s->stream);
+        if (stats) cudaEventRecord(ev[4 * t + 3], s->stream);
         st = s->solver.record(s->ctl_log + t);
         s->step += 1;
     }
@@ -491,8 +504,9 @@ gbsw_status les_step(gbsw_les *s, int nsteps, gbsw_les_stats *stats)
             stats[t].iters = c.iters;
             stats[t].status = one;
             stats[t].rel_res = c.rho;
-            cudaEventElapsedTime(&stats[t].ms_predictor, ev[3 * t], ev[3 * t + 1]);
-            cudaEventElapsedTime(&stats[t].ms_solve, ev[3 * t + 1], ev[3 * t + 2]);
+            cudaEventElapsedTime(&stats[t].ms_predictor, ev[4 * t], ev[4 * t + 1]);
+            cudaEventElapsedTime(&stats[t].ms_guess, ev[4 * t + 1], ev[4 * t + 2]);
+            cudaEventElapsedTime(&stats[t].ms_solve, ev[4 * t + 2], ev[4 * t + 3]);
         }
         if (one < 0 && worst >= 0) worst = one;
         else if (one == GBSW_NOT_CONVERGED && worst == GBSW_OK) worst = one;
@@ -548,6 +562,14 @@ gbsw_status les_set_step(gbsw_les *s, int step)
 {
     if (!s || step < 0) return GBSW_ERR_ARG;
     s->step = step;
+    return GBSW_OK;
+}
+
+gbsw_status les_set_warm_start(gbsw_les *s, gbsw_unet *net)
+{
+    if (!s) return GBSW_ERR_ARG;
+    if (net && (s->q.d.nz % 4 || s->q.d.ny % 4 || s->q.d.nx % 4)) return GBSW_ERR_ARG;
+    s->net = net;
     return GBSW_OK;
 }
 

@@ -39,7 +39,7 @@ class LES:
         if not stats:
             return st
         return [dict(iters=a.iters, status=a.status, rel_res=a.rel_res, ms_predictor=a.ms_predictor,
-                     ms_solve=a.ms_solve) for a in arr[:nsteps]]
+                     ms_solve=a.ms_solve, ms_guess=a.ms_guess) for a in arr[:nsteps]]
 
     def get(self, name: str) -> np.ndarray:
         nz, ny, nx = self.shape
@@ -71,6 +71,13 @@ class LES:
         p.max_iter = p.max_iter if max_iter is None else int(max_iter)
         p.check_every = p.check_every if check_every is None else int(check_every)
         N.check(N.lib().les_set_solver(self._h, p.omega, p.tol, p.max_iter, p.check_every), "les_set_solver")
+
+    def set_warm_start(self, net):
+        """Use a UNet (paper_1711_04471_gb300.unet.UNet) as the pressure warm
+        start, or None for the previous pressure.  The network must outlive
+        its use here."""
+        self._net = net
+        N.check(N.lib().les_set_warm_start(self._h, None if net is None else net._h), "les_set_warm_start")
 
     def set_fixed_iterations(self, niter: int):
         """Paper mode: exactly niter SOR iterations per step (0 = tolerance-driven)."""

@@ -1,0 +1,100 @@
+"""The GPU U-Net (tcgen05 convolutions, BF16 activations, FP32 accumulation)
+against the FP64 oracle network with the same parameters.
+
+BF16 rounding of every activation bounds the agreement: relative L2 error of
+the output <= 3e-2, gradients aligned (cosine >= 0.99) and within 10 % per
+layer.  Training must reduce the loss; the LES with the network as warm
+start still converges to the same tolerance (the solve decides the answer).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import unet as OU
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def U():
+    import paper_1711_04471_gb300 as P
+    P.build()
+    from paper_1711_04471_gb300 import unet
+    oracle.lib()
+    return unet
+
+
+def bf16(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(torch.bfloat16).float().numpy()
+
+
+def sample(rng, n, D, H, W):
+    x = bf16(rng.standard_normal((n, D, H, W, 2)))
+    t = rng.standard_normal((n, D, H, W)).astype(np.float32) * 0.5
+    return x, t
+
+
+def test_forward_matches_oracle(U):
+    import torch
+    rng = np.random.default_rng(0)
+    x, _ = sample(rng, 2, 4, 32, 64)
+    with U.UNet(seed=3) as net:
+        P = U.unflatten(bf16(net.get_params()).astype(np.float64))
+        net.set_params(U.flatten(P))
+        y = net.forward(torch.from_numpy(x).cuda()).cpu().numpy()
+    for k in range(2):
+        ref, _ = OU.forward(P, x[k].astype(np.float64))
+        err = np.linalg.norm(y[k] - ref[..., 0]) / np.linalg.norm(ref)
+        assert err <= 3e-2, err
+
+
+def test_gradients_match_oracle(U):
+    import torch
+    rng = np.random.default_rng(1)
+    x, t = sample(rng, 1, 4, 32, 64)
+    with U.UNet(seed=5) as net:
+        P = U.unflatten(bf16(net.get_params()).astype(np.float64))
+        net.set_params(U.flatten(P))
+        loss, g = net.gradients(torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda())
+    out, c = OU.forward(P, x[0].astype(np.float64))
+    lo, dout = OU.mse(out, t[0][..., None].astype(np.float64))
+    Go = OU.backward(P, c, dout)
+    assert abs(loss - lo) <= 3e-2 * lo
+    Gg = U.unflatten(g.astype(np.float64))
+    for name in Go:
+        a, b = Gg[name].ravel(), Go[name].ravel()
+        cos = a @ b / (np.linalg.norm(a) * np.linalg.norm(b) + 1e-300)
+        rel = np.linalg.norm(a - b) / (np.linalg.norm(b) + 1e-300)
+        assert cos >= 0.99 and rel <= 0.1, (name, cos, rel)
+
+
+def test_training_reduces_loss(U):
+    import torch
+    rng = np.random.default_rng(2)
+    x = torch.from_numpy(bf16(rng.standard_normal((2, 8, 32, 64, 2)))).cuda()
+    # a smooth target that depends on the input: a blurred copy of channel 0
+    xc = x[..., 0]
+    t = (xc + torch.roll(xc, 1, 3) + torch.roll(xc, -1, 3) + torch.roll(xc, 1, 2) + torch.roll(xc, -1, 2)) / 5.0
+    t = t.contiguous()
+    with U.UNet(seed=7) as net:
+        losses = [net.train_step(x, t, 2e-3) for _ in range(60)]
+    assert losses[-1] < 0.5 * losses[0], (losses[0], losses[-1])
+
+
+def test_les_with_learned_warm_start_converges(U):
+    from paper_1711_04471_gb300 import inputs
+    from paper_1711_04471_gb300.les import LES
+    nx, ny, nz = 64, 32, 16
+    solid = inputs.les_buildings(nx, ny, nz, dx=4.0, seed=11, margin_cells=4)
+    with U.UNet(seed=1) as net, LES(nx, ny, nz, solid) as plain, LES(nx, ny, nz, solid) as warm:
+        warm.set_warm_start(net)
+        sp = plain.step(3)
+        sw = warm.step(3)
+        for a in sw:
+            assert a["status"] == 0 and a["rel_res"] <= 1e-6 and a["ms_guess"] > 0
+        # both solves reach the tolerance, so the pressures agree to it
+        pa, pb = plain.get("p")[1:-1, 1:-1, 1:-1], warm.get("p")[1:-1, 1:-1, 1:-1]
+        assert np.linalg.norm(pa - pb) / np.linalg.norm(pa) < 1e-3
+        warm.set_warm_start(None)
+        assert warm.step(1)[0]["ms_guess"] < 0.05
