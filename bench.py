@@ -1,4 +1,10 @@
-"""Benchmark of the 2DSW time step (4096 x 4096 wet/dry workload, FP32).
+"""Benchmarks of the 2DSW and UFLES time steps.
+
+Default workload (the headline line): the 2DSW time step on the 4096 x 4096
+wet/dry grid, FP32.  Other workloads (--workload): ``ensemble`` (512
+instances, persistent kernel vs separate launches), ``les`` (256x256x128
+UFLES step at 1e-6 residual) and ``les-nn`` (the same, learned warm start
+vs previous-pressure warm start on the same states).
 
 One benchmark step = 100 model time steps of the 4096^2 grid (the fused
 momentum / continuity / Shapiro / update kernel, temporally blocked) plus
@@ -31,6 +37,10 @@ N_CELLS_SIDE = 4096
 STEPS_PER_BENCH_STEP = 100
 BYTES_PER_CELL_UPDATE = 28  # read eta, u, v, H; write eta, u, v (FP32)
 METRIC = "cell-updates/s"
+# DRAM bytes (read + write) of one sw_stream_kernel<3> launch on the 4096^2
+# grid, from the ncu capture summarised in profiles/sw_stream_kernel_4096.md;
+# set to None whenever that kernel changes until it is captured again.
+TRAFFIC_SW_STREAM_T3 = 458.705664e6
 WORKLOAD = "2DSW 4096x4096 wet/dry (15% dry), FP32, 100 time steps + FP64 volume per step"
 
 
@@ -254,7 +264,9 @@ def run_gbsw(args, rank, world, local):
                    "steps_per_launch": T, "l2": "state 268 MB > 129 MB L2, no flush needed",
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": peak, "unit": "GB/s",
-                     "frac": achieved_gbs / peak, "traffic": args.traffic,
+                     "frac": achieved_gbs / peak,
+                     "traffic": args.traffic if args.traffic is not None else
+                     (TRAFFIC_SW_STREAM_T3 if T == 3 else None),
                      "peak_kind": peak_kind, "kernel": "sw_stream_kernel",
                      "per_unit": f"{BYTES_PER_CELL_UPDATE} B/cell-update x {T} steps x {cells} cells per launch",
                      "compulsory_gbs": compulsory_gbs, "compulsory_frac": compulsory_gbs / peak,
@@ -270,8 +282,175 @@ def run_gbsw(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+def _timed_region(fn, world):
+    """Barrier + synchronize on both sides of fn(); returns seconds (max over ranks)."""
+    import torch
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    fn()
+    torch.cuda.synchronize()
+    barrier(world)
+    return max_over_ranks(time.perf_counter() - t0, world)
+
+
+def run_ensemble(args, rank, world, local):
+    """512 2DSW instances (sides log-uniform in [64, 1024]), 100 time steps per
+    bench step: one persistent cooperative kernel per call (CUDA graph) vs one
+    launch per instance and fused level."""
+    import torch
+
+    import paper_1711_04471_gb300 as P
+    from paper_1711_04471_gb300 import inputs
+    from paper_1711_04471_gb300.sw import SWBatch
+    P.build()
+    torch.cuda.set_device(local)
+    sizes = inputs.sw_ensemble_sizes(512, seed=1002)
+    members = [inputs.sw_ensemble_member(int(n), 1002, k) for k, n in enumerate(sizes)]
+    cells = int(sum(int(n) * int(n) for n in sizes))
+    stream = torch.cuda.current_stream()
+    b = SWBatch(members, stream=stream)
+    T, rows = b.autotune(trial_steps=12, cache_path=os.environ.get("GBSW_TUNE_CACHE"))
+    per = STEPS_PER_BENCH_STEP
+    for _ in range(args.warmup):
+        b.step(per)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    t_graph = _timed_region(lambda: [b.step(per) for _ in range(args.steps)], world)
+    clk = clocks.stop()
+    vols, _ = b.volumes()
+    for _ in range(max(1, args.warmup // 2)):
+        b.step_separate(per)
+    t_sep = _timed_region(lambda: [b.step_separate(per) for _ in range(args.steps)], world)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        b.step(per)
+        b.volumes()          # per-step FP64 volumes read back to the host
+    t_e2e = max_over_ranks(time.perf_counter() - t0, world)
+    b.close()
+    if rank != 0:
+        return
+    value = cells * per * args.steps * world / t_graph
+    peak, peak_kind = _peaks()
+    levels = per // T + (1 if per % T else 0)
+    level_s = t_graph / (args.steps * levels)
+    ach = BYTES_PER_CELL_UPDATE * cells * T / level_s / 1e9
+    line = {"metric": "ensemble cell-updates/s", "value": value, "unit": "cell-updates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_graph / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "2DSW ensemble: 512 instances, sides log-uniform 64..1024, "
+                                   f"{cells} cells, 100 time steps + FP64 volumes per step",
+                       "tiling": {"steps_per_level": T, "rows_per_item": rows}},
+            "separate_launches": {"value": cells * per * args.steps * world / t_sep, "unit": "cell-updates/s",
+                                  "ms_per_step": t_sep / args.steps * 1e3},
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                         "traffic": None, "peak_kind": peak_kind, "kernel": "sw_batch_kernel",
+                         "per_unit": f"{BYTES_PER_CELL_UPDATE} B/cell-update x {T} steps x {cells} cells per level"},
+            "e2e": {"value": cells * per * args.steps / t_e2e, "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 8 * 3 * 512},
+            "gpu_launches": args.steps, "clocks": clk, "volume_min": float(min(vols))}
+    print(json.dumps(line), flush=True)
+
+
+def _les_cpu_sample(shape, solid, sor_iters=20):
+    """Oracle (FP64, one thread) on the full grid: one predictor pass and
+    sor_iters SOR iterations, timed separately."""
+    import ctypes as C
+
+    import oracle
+    from oracle import les as ol
+    nx, ny, nz = shape
+    Pm = ol.make_params(nx, ny, nz)
+    st = ol.LESState(Pm, solid)
+    L = oracle.lib()
+    t0 = time.perf_counter()
+    ol.velnw(Pm, st.p, st.u, st.v, st.w)
+    ol.bondv1(Pm, st.u, st.v, st.w)
+    fu, fv, fw = ol.velfg(Pm, st.u, st.v, st.w)
+    ol.feedbf(Pm, solid, st.u, st.v, st.w, st.gu, st.gv, st.gw, fu, fv, fw)
+    nt = ol.nut(Pm, st.u, st.v, st.w)
+    ol.visc(Pm, st.u, st.v, st.w, nt, fu, fv, fw)
+    ol.adam(Pm, True, st.u, st.v, st.w, fu, fv, fw, st.fuo, st.fvo, st.fwo)
+    b = ol.rhs(Pm, st.u, st.v, st.w)
+    t_pred = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ol.sor(Pm, b, st.p, tol=0.0, max_iter=sor_iters)
+    t_iter = (time.perf_counter() - t0) / sor_iters
+    return t_pred, t_iter
+
+
+def run_les(args, rank, world, local, learned):
+    """UFLES 256x256x128 (20 % building cover), SOR omega 1.8 to a 1e-6
+    relative FP64 residual, 20 spin-up steps excluded.  With learned=True each
+    timed state is stepped twice: previous-pressure warm start and the U-Net."""
+    import numpy as np
+    import torch
+
+    import paper_1711_04471_gb300 as P
+    from paper_1711_04471_gb300 import inputs
+    from paper_1711_04471_gb300.les import LES
+    P.build()
+    torch.cuda.set_device(local)
+    shape = (256, 256, 128)
+    solid = inputs.les_buildings(*shape, dx=4.0, seed=1003)
+    kw = dict(check_every=50, max_iter=400000)
+    rows = []
+    if learned:
+        from paper_1711_04471_gb300 import train_unet
+        from paper_1711_04471_gb300.unet import UNet
+        net = UNet(seed=0)
+        net.set_params(np.load(args.weights))
+        rows = train_unet.compare_warm_starts(net, shape=shape, spinup=args.spinup, steps=args.steps,
+                                              log=lambda *a: None, **kw)
+        net.close()
+        t_plain = sum(r["plain_ms"] for r in rows) / len(rows)
+        t_nn = sum(r["nn_ms"] for r in rows) / len(rows)
+    else:
+        with LES(*shape, solid, **kw) as g:
+            g.step(args.spinup, stats=False)
+            st = g.step(args.steps)
+        rows = [dict(plain_iters=a["iters"], plain_ms=a["ms_predictor"] + a["ms_solve"],
+                     pred_ms=a["ms_predictor"], solve_ms=a["ms_solve"], res=a["rel_res"]) for a in st]
+        t_plain = sum(r["plain_ms"] for r in rows) / len(rows)
+    if rank != 0:
+        return
+    cells = shape[0] * shape[1] * shape[2]
+    iters = sum(r["plain_iters"] for r in rows) / len(rows)
+    peak, peak_kind = _peaks()
+    solve_ms = (sum(r.get("solve_ms", r["plain_ms"]) for r in rows) / len(rows))
+    per_iter_s = solve_ms * 1e-3 / max(iters, 1)
+    ach = 12.0 * cells / per_iter_s / 1e9      # 12 B/cell/iteration: correction in+out, residual in
+    t_pred, t_iter = _les_cpu_sample(shape, solid) if (world == 1 and not args.no_cpu_baseline) else (None, None)
+    line = {"metric": "LES step time at 1e-6 residual" + (" (learned warm start)" if learned else ""),
+            "value": t_nn if learned else t_plain, "unit": "ms/step", "n_gpus": world, "steps": args.steps,
+            "warmup": args.spinup, "ms_per_step": t_nn if learned else t_plain, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 sweeps, f64 pressure and norms",
+            "data": "synthetic",
+            "config": {"workload": "UFLES 256x256x128, dx 4 m, dt 0.025 s, 20 % building cover, SOR omega 1.8, "
+                                   "tol 1e-6 (FP64), warm start " + ("U-Net vs previous pressure" if learned
+                                                                     else "previous pressure"),
+                       "spinup_steps": args.spinup},
+            "sor_iters_per_step": iters,
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                         "traffic": None, "peak_kind": peak_kind, "kernel": "sor_sweep_kernel",
+                         "per_unit": "12 B/cell/iteration x 8388608 cells (solve time / iterations)"},
+            "cpu_baseline": None if t_pred is None else {
+                "value": (t_pred + iters * t_iter) * 1e3, "unit": "ms/step", "cores": 1, "kind": "oracle",
+                "sample": f"one predictor pass + 20 SOR iterations on the full grid (FP64, 1 thread), "
+                          f"step time extrapolated to {iters:.0f} iterations"},
+            "rows": rows}
+    if learned:
+        line["plain"] = {"ms_per_step": t_plain, "sor_iters_per_step": iters}
+        line["learned"] = {"ms_per_step": t_nn, "sor_iters_per_step": sum(r["nn_iters"] for r in rows) / len(rows),
+                           "guess_ms": sum(r["nn_guess_ms"] for r in rows) / len(rows)}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="sw4096", choices=["sw4096", "ensemble", "les", "les-nn"])
+    ap.add_argument("--spinup", type=int, default=20)
+    ap.add_argument("--weights", default=os.path.join(ROOT, "paper_1711_04471_gb300", "data", "unet_warmstart.npy"))
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=5)
@@ -285,6 +464,10 @@ def main():
     rank, world, local = dist_setup(args.gpus)
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == "ensemble":
+        run_ensemble(args, rank, world, local)
+    elif args.workload in ("les", "les-nn"):
+        run_les(args, rank, world, local, learned=args.workload == "les-nn")
     else:
         run_gbsw(args, rank, world, local)
     if world > 1:
