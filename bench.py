@@ -446,9 +446,78 @@ def run_les(args, rank, world, local, learned):
     print(json.dumps(line), flush=True)
 
 
+def run_sw_paper(args, rank, world, local):
+    """The paper's 2DSW sizes (Sec. 6.2): 500^2, 1000^2, 2000^2 cells, dx = 1 m,
+    dt = 0.01 s, 10 000 steps; flat 10 m basin with a Gaussian hump (the
+    textbook basin itself is not available)."""
+    import torch
+
+    import paper_1711_04471_gb300 as P
+    from paper_1711_04471_gb300 import inputs
+    from paper_1711_04471_gb300.sw import SW
+    P.build()
+    torch.cuda.set_device(local)
+    res = []
+    for n in (500, 1000, 2000):
+        inp = inputs.sw_hump(n=n, dx=1.0, dt=0.01, sigma_cells=n / 20.0)
+        with SW(inp.params(), inp.H, inp.eta0, stream=torch.cuda.current_stream()) as g:
+            g.step(300)
+            g.volume()
+            t = _timed_region(lambda: (g.step(10000), g.volume()), world)
+        cpu = None
+        if not args.no_cpu_baseline:
+            import oracle
+            o = oracle.SWState(inp.params(), inp.H, inp.eta0)
+            steps = max(1, int(2e7 // (n * n)))
+            t0 = time.perf_counter()
+            o.run(steps)
+            cpu = n * n * steps / (time.perf_counter() - t0)
+        res.append({"n": n, "seconds_10000_steps": t, "cell_updates_per_s": n * n * 10000 / t,
+                    "oracle_cell_updates_per_s_1thread": cpu})
+    if rank != 0:
+        return
+    big = res[-1]
+    print(json.dumps({"metric": "cell-updates/s (paper 2DSW sizes)", "value": big["cell_updates_per_s"],
+                      "unit": "cell-updates/s", "n_gpus": world, "steps": 10000, "warmup": 300,
+                      "ms_per_step": big["seconds_10000_steps"] / 10, "higher_is_better": True, "scaling": "weak",
+                      "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                      "config": {"workload": "2DSW at the paper's sizes, dx 1 m, dt 0.01 s, 10000 steps"},
+                      "sizes": res}), flush=True)
+
+
+def run_les_paper(args, rank, world, local):
+    """The paper's UFLES setup (Sec. 6.3.2): 300x300x90 cells, 50 SOR
+    iterations per step, dt = 0.025 s over 1.2 km; per-phase device times."""
+    import torch
+
+    import paper_1711_04471_gb300 as P
+    from paper_1711_04471_gb300 import inputs
+    from paper_1711_04471_gb300.les import LES
+    P.build()
+    torch.cuda.set_device(local)
+    shape = (300, 300, 90)
+    solid = inputs.les_buildings(*shape, dx=4.0, seed=1004)
+    with LES(*shape, solid) as g:
+        g.set_fixed_iterations(50)
+        g.step(args.spinup, stats=False)
+        st = g.step(args.steps)
+    pred = sum(a["ms_predictor"] for a in st) / len(st)
+    solve = sum(a["ms_solve"] for a in st) / len(st)
+    if rank != 0:
+        return
+    print(json.dumps({"metric": "LES step time, 50 SOR iterations (paper setup)", "value": pred + solve,
+                      "unit": "ms/step", "n_gpus": world, "steps": args.steps, "warmup": args.spinup,
+                      "ms_per_step": pred + solve, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+                      "dtype": "f32 sweeps, f64 pressure", "data": "synthetic",
+                      "config": {"workload": "UFLES 300x300x90, dx 4 m, dt 0.025 s, fixed 50 SOR iterations"},
+                      "breakdown_ms": {"velnw..adam+rhs": pred, "press": solve},
+                      "press_share": solve / (pred + solve),
+                      "final_rel_res": sum(a["rel_res"] for a in st) / len(st)}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="sw4096", choices=["sw4096", "ensemble", "les", "les-nn"])
+    ap.add_argument("--workload", default="sw4096", choices=["sw4096", "ensemble", "les", "les-nn", "sw-paper", "les-paper"])
     ap.add_argument("--spinup", type=int, default=20)
     ap.add_argument("--weights", default=os.path.join(ROOT, "paper_1711_04471_gb300", "data", "unet_warmstart.npy"))
     ap.add_argument("--gpus", type=int, default=1)
@@ -466,6 +535,10 @@ def main():
         run_reference(args, rank, world)
     elif args.workload == "ensemble":
         run_ensemble(args, rank, world, local)
+    elif args.workload == "sw-paper":
+        run_sw_paper(args, rank, world, local)
+    elif args.workload == "les-paper":
+        run_les_paper(args, rank, world, local)
     elif args.workload in ("les", "les-nn"):
         run_les(args, rank, world, local, learned=args.workload == "les-nn")
     else:

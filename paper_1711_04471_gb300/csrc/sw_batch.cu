@@ -448,11 +448,26 @@ gbsw_status sw_batch_step_separate(gbsw_sw_batch *b, int nsteps)
     while (left > 0) {
         const int T = std::min(left, b->T);
         const int a = b->cur, c = 1 - b->cur;
+        static int per_sm[5] = {0, 0, 0, 0, 0};
+        if (per_sm[T] == 0) {
+            int v = 0;
+            switch (T) {
+            case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, sw_stream_kernel<1>, SWS_THREADS, 0); break;
+            case 2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, sw_stream_kernel<2>, SWS_THREADS, 0); break;
+            case 3: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, sw_stream_kernel<3>, SWS_THREADS, 0); break;
+            default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, sw_stream_kernel<4>, SWS_THREADS, 0); break;
+            }
+            per_sm[T] = std::max(1, v);
+        }
         for (int m = 0; m < b->n; ++m) {
             const SWInst &I = b->inst_h[m];
             const int W = SWS_THREADS - 4 * T;
-            const int rows = b->rows;
-            dim3 grid(ceil_div(I.p.nx, W), ceil_div(I.p.ny, rows));
+            // each launch sized to fill the GPU on its own, as sw_step does
+            const int strips = ceil_div(I.p.nx, W);
+            int segments = std::max(1, per_sm[T] * sm_count() / strips);
+            segments = std::min(segments, std::max(1, I.p.ny / (8 * T)));
+            const int rows = ceil_div(I.p.ny, segments);
+            dim3 grid(strips, ceil_div(I.p.ny, rows));
 #define SEP_LAUNCH(TT)                                                                                         \
     sw_stream_kernel<TT><<<grid, SWS_THREADS, 0, b->stream>>>(I.p, rows, b->H + I.off, b->eta[a] + I.off,          \
                                                               b->u[a] + I.off, b->v[a] + I.off, b->eta[c] + I.off, \
