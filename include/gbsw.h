@@ -54,6 +54,14 @@ int gbsw_version(void);
  * if none). */
 const char *gbsw_last_error(void);
 
+/* Self-test of the bounded device-side waits (the paper has no
+ * counterpart).  which = 0 waits on an mbarrier phase that never completes
+ * for `budget` clock cycles, which = 1 spins on a flag that is never set
+ * for `budget` iterations; 1 <= budget <= 1e9.  Returns GBSW_ERR_TIMEOUT
+ * when the wait gave up as designed, leaving the context usable.
+ * Synchronous. */
+gbsw_status gbsw_selftest_wait(int which, long long budget);
+
 /* ------------------------------------------------------------------------
  * 2-D shallow water (Sec. 6.2: time loop of predictor "dyn", first-order
  * Shapiro filter "shapiro", then the velocity/state update).

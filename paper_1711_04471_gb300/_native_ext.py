@@ -48,5 +48,6 @@ def declare(L, sig):
     sig(L, "unet_train_step", C.c_int, [vp, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, C.c_float, dp])
     sig(L, "unet_destroy", None, [vp])
     sig(L, "les_set_warm_start", C.c_int, [vp, vp])
+    sig(L, "gbsw_selftest_wait", C.c_int, [C.c_int, C.c_longlong])
     sig(L, "poisson_solve", C.c_int, [C.c_int, C.c_int, C.c_int, C.c_double, vp, vp, C.c_double, C.c_double,
                                       C.c_int, C.c_int, vp, ip, dp])

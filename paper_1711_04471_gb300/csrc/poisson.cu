@@ -150,7 +150,7 @@ poisson_test_kernel(const double *__restrict__ partials, int nblocks, PoissonCtl
         ctl->bb = bb;
         const double rho = bb > 0.0 ? sqrt(rr / bb) : 0.0;
         ctl->rho = rho;
-        const bool bad = !isfinite(rho);
+        const bool bad = !isfinite(rr) || !isfinite(bb) || !isfinite(rho);  // a NaN b must not look converged
         if (bad) ctl->status = DEV_NONFINITE;
         const bool done = bad || bb < 1e-60 || rho <= tol || ctl->iters >= max_iter;
         ctl->done = done ? 1 : 0;
