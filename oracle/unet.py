@@ -12,8 +12,9 @@ skip connections by channel concatenation [upsampled, skip]):
     up, cat s1 (32), l1c 32->16                   (full)
     head: 1x1x1 16->1, no activation
 
-Input channels: [b * dx^2 / s, p_prev / s]; output: (p - p_prev) / s,
-with s a per-sample scale (the standard deviation of b * dx^2).
+Two input channels, one output channel; what they hold for the learned
+warm start (coarse residual and pressure in, scaled coarse increment out)
+is defined in oracle/warmstart.py.
 """
 from __future__ import annotations
 
