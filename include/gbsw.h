@@ -308,7 +308,8 @@ gbsw_status poisson_solve(int nx, int ny, int nz, double dx, float *p, const flo
  *         mask > 0, else 0 (mask: device FP32, same shape as y)
  *   y     device, nsamples*D*H*W*cout FP32 (the FP32 accumulator, unrounded)
  * cin, cout in {16, 32, 64} (pairs used by the network); W a power of two
- * of at least 16 or a multiple of 128; H a multiple of 128/min(W, 128).
+ * or a multiple of 128.  With m = 128/min(W, 128): H a multiple of m, or
+ * H a power of two below m with W*H >= 16 (a tile then spans m/H planes).
  * Synchronous; allocates a temporary BF16 copy of x and the packed weights.
  */
 gbsw_status unet_conv3d(int nsamples, int D, int H, int W, int cin, int cout, const float *x, const float *w,
@@ -330,10 +331,11 @@ gbsw_status unet_get_params(gbsw_unet *net, float *host, int n);
 gbsw_status unet_set_params(gbsw_unet *net, const float *host, int n);
 
 /*
- * Forward pass.  x: device, n*D*H*W*2 FP32 (channels last: the scaled
- * right-hand side and previous pressure); y: device, n*D*H*W FP32 (the
- * scaled pressure increment).  D, H, W multiples of 4, W/4 a power of two
- * >= 16 (or a multiple of 128).  Synchronous.
+ * Forward pass.  x: device, n*D*H*W*2 FP32 (channels last; for the warm
+ * start the features of warm_start_features); y: device, n*D*H*W FP32.
+ * D, H, W multiples of 4; each level (1, 1/2, 1/4) must meet the geometry
+ * rule of unet_conv3d (e.g. 16x16x8, whose levels are 16x16, 8x8, 4x4
+ * planes).  Synchronous.
  */
 gbsw_status unet_forward(gbsw_unet *net, int n, int D, int H, int W, const float *x, float *y);
 
@@ -350,13 +352,51 @@ gbsw_status unet_train_step(gbsw_unet *net, int n, int D, int H, int W, const fl
 void unet_destroy(gbsw_unet *net);
 
 /*
- * Learned warm start for les_step: before each pressure solve the network
- * maps [b dx^2 / s, p_prev / s] (s = dx^2 rms(b)) to an increment that is
- * added to the previous pressure; SOR then runs to the same tolerance.
+ * Learned warm start for les_step (the "press" step of Sec. 6.3.1 keeps its
+ * SOR; only the initial guess changes).  Before each solve the network runs
+ * on the grid coarsened by a factor f, where its receptive field spans the
+ * domain (the smooth modes that set the SOR iteration count are global):
+ * the input is warm_start_features of the right-hand side b and the
+ * previous pressure, and the prolongated, rescaled output is added to the
+ * previous pressure (warm_start_apply).  SOR then runs to the same
+ * tolerance, so the plain solve still decides the answer.
  * net = NULL restores the plain warm start (previous pressure).  The
  * context does not own the network; keep it alive while it is set.
+ * GBSW_ERR_ARG if the network does not fit the coarse grid (see
+ * les_set_warm_start_factor).
  */
 gbsw_status les_set_warm_start(gbsw_les *les, gbsw_unet *net);
+
+/* Coarsening factor f of the warm start: a power of two dividing nx, ny,
+ * nz such that the coarse grid meets unet_forward's shape rule, or 0 for
+ * the default (the largest such f <= 16; 16 on a 256 x 256 x 128 grid,
+ * whose coarse grid is 16 x 16 x 8).  GBSW_ERR_ARG otherwise. */
+gbsw_status les_set_warm_start_factor(gbsw_les *les, int f);
+
+/*
+ * Network input of the warm start, on caller-owned device arrays:
+ *   p      device, nz*ny*nx FP64, the previous pressure (dense, x fastest)
+ *   b      device, nz*ny*nx FP32, the right-hand side (divergence / dt)
+ *   x      device, out: (nz/f)(ny/f)(nx/f) x 2 FP32, channels last:
+ *          [r_c / rms(r_c), p_c / rms(p_c)], r_c and p_c the block means over
+ *          f^3 cells of r = b - A p and of p (A: the operator of poisson_solve)
+ *   scale  host, out: s = (f dx)^2 rms(r_c), the unit of the network's output
+ * f a power of two dividing nx, ny, nz.  Block sums in FP64, fixed order.
+ * Synchronous.  The training target for a converged pressure p_new is the
+ * block mean of (p_new - p) / s.
+ */
+gbsw_status warm_start_features(int nx, int ny, int nz, double dx, int f, const double *p, const float *b,
+                                float *x, double *scale, void *stream);
+
+/*
+ * p += scale * prolong(out): out device (nz/f)(ny/f)(nx/f) FP32, p device
+ * nz*ny*nx FP64 (dense).  prolong is trilinear between coarse cell centres,
+ * holding the end values at the inflow, ground and lid, with the ghost
+ * past the outflow equal to minus the last value (p = 0 on that face) and
+ * wrapping in y.  Synchronous.
+ */
+gbsw_status warm_start_apply(int nx, int ny, int nz, int f, const float *out, double scale, double *p,
+                             void *stream);
 
 /*
  * Volume reduction that allocates no memory.  The paper has no

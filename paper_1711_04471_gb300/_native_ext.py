@@ -48,6 +48,9 @@ def declare(L, sig):
     sig(L, "unet_train_step", C.c_int, [vp, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, C.c_float, dp])
     sig(L, "unet_destroy", None, [vp])
     sig(L, "les_set_warm_start", C.c_int, [vp, vp])
+    sig(L, "les_set_warm_start_factor", C.c_int, [vp, C.c_int])
+    sig(L, "warm_start_features", C.c_int, [C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, vp, vp, vp, dp, vp])
+    sig(L, "warm_start_apply", C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, vp, C.c_double, vp, vp])
     sig(L, "gbsw_selftest_wait", C.c_int, [C.c_int, C.c_longlong])
     sig(L, "poisson_solve", C.c_int, [C.c_int, C.c_int, C.c_int, C.c_double, vp, vp, C.c_double, C.c_double,
                                       C.c_int, C.c_int, vp, ip, dp])

@@ -26,6 +26,7 @@
 
 #include "poisson.cuh"
 #include "unet_ops.cuh"
+#include "warmstart.cuh"
 
 using namespace gbsw;
 
@@ -293,10 +294,28 @@ struct gbsw_les {
     int step;
     int fixed_iters;       // > 0: paper mode, exactly this many SOR iterations per step
     gbsw_unet *net;        // learned warm start (not owned), NULL = previous pressure
+    int ws_factor;         // the network runs on the grid coarsened by this factor (0 = default)
     size_t n;              // elements per padded field
 };
 
 namespace {
+
+// True if the network fits the grid coarsened by f.
+bool ws_fits(const gbsw_les *s, int f)
+{
+    const int nx = s->q.d.nx, ny = s->q.d.ny, nz = s->q.d.nz;
+    return ws_factor_ok(nx, ny, nz, f) && unet_shape_ok(nz / f, ny / f, nx / f);
+}
+
+// Coarsening factor of the learned warm start: the one set, else the
+// largest power of two <= 16 at which the network fits the coarse grid.
+int ws_factor_of(const gbsw_les *s)
+{
+    if (s->ws_factor > 0) return s->ws_factor;
+    for (int f = 16; f > 1; f >>= 1)
+        if (ws_fits(s, f)) return f;
+    return 1;
+}
 
 gbsw_status les_alloc(gbsw_les *s)
 {
@@ -476,7 +495,7 @@ gbsw_status les_step(gbsw_les *s, int nsteps, gbsw_les_stats *stats)
         if (st != GBSW_OK) break;
         if (stats) cudaEventRecord(ev[4 * t + 1], s->stream);
         if (s->net) {
-            st = unet_warm_start(s->net, s->b, s->solver.p_hi, pd, s->p.dx, s->stream);
+            st = unet_warm_start(s->net, s->b, s->solver.p_hi, pd, s->p.dx, ws_factor_of(s), s->stream);
             if (st != GBSW_OK) break;
         }
         if (stats) cudaEventRecord(ev[4 * t + 2], s->stream);
@@ -568,8 +587,15 @@ gbsw_status les_set_step(gbsw_les *s, int step)
 gbsw_status les_set_warm_start(gbsw_les *s, gbsw_unet *net)
 {
     if (!s) return GBSW_ERR_ARG;
-    if (net && (s->q.d.nz % 4 || s->q.d.ny % 4 || s->q.d.nx % 4)) return GBSW_ERR_ARG;
+    if (net && !ws_fits(s, ws_factor_of(s))) return GBSW_ERR_ARG;
     s->net = net;
+    return GBSW_OK;
+}
+
+gbsw_status les_set_warm_start_factor(gbsw_les *s, int f)
+{
+    if (!s || f < 0 || (f != 0 && !ws_fits(s, f))) return GBSW_ERR_ARG;
+    s->ws_factor = f;
     return GBSW_OK;
 }
 

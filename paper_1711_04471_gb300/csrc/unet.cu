@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "unet_ops.cuh"
+#include "warmstart.cuh"
 
 using namespace gbsw;
 
@@ -45,6 +46,7 @@ struct Acts {
     ConvGeom g[3];             // levels 1..3
     long long nvox;            // full-resolution voxels
     float *xin = nullptr, *out = nullptr;
+    double *ws = nullptr;      // warm start: block means r_c, p_c (nvox each) and the scale
     bf16 *a1a, *u1, *p1, *a2a, *u2, *p2, *a3a, *b3, *d2, *d1;
     bf16 *g_d1 = nullptr, *g_u1, *g_d2, *g_u2, *g_b3, *g_a3a, *g_p2, *g_s2, *g_a2a, *g_p1, *g_s1, *g_a1a;
     CUtensorMap m_fwd[NLAYERS];  // input map of each layer's forward conv (l1a unused)
@@ -63,7 +65,7 @@ struct gbsw_unet {
     bool packs_dirty;
     int adam_step;
     int *status;
-    double *loss, *sumsq;
+    double *loss;
     cudaStream_t stream;
     std::map<std::tuple<int, int, int, int>, Acts *> acts;
 };
@@ -109,6 +111,7 @@ gbsw_status make_acts(int N, int D, int H, int W, bool train, Acts **out)
     };
     if (st == GBSW_OK) st = alloc(a, &a->xin, (size_t)v1 * 2);
     if (st == GBSW_OK) st = alloc(a, &a->out, (size_t)v1);
+    if (st == GBSW_OK && N == 1) st = alloc(a, &a->ws, (size_t)(2 * v1 + 1));
     B(&a->a1a, v1, 16);
     B(&a->u1, v1, 32);
     B(&a->p1, v2, 16);
@@ -305,13 +308,29 @@ struct HostRng {
 
 // Hook used by the LES step (declared in unet_ops.cuh's companion below).
 namespace gbsw {
-gbsw_status unet_warm_start(gbsw_unet *u, const float *b, double *p, const PadDims &pd, double dx, cudaStream_t s)
+bool unet_shape_ok(int D, int H, int W)
 {
+    if (D < 4 || H < 4 || W < 4 || D % 4 || H % 4 || W % 4) return false;
+    ConvGeom g;
+    for (int l = 0; l < 3; ++l) {
+        const int s = 1 << l;
+        if (conv_geometry(D / s, D / s, H / s, W / s, &g) != GBSW_OK) return false;
+    }
+    return true;
+}
+
+gbsw_status unet_warm_start(gbsw_unet *u, const float *b, double *p, const PadDims &pd, double dx, int f,
+                            cudaStream_t s)
+{
+    if (!ws_factor_ok(pd.nx, pd.ny, pd.nz, f)) return GBSW_ERR_ARG;
     Acts *a = nullptr;
-    TRY(get_acts(u, 1, pd.nz, pd.ny, pd.nx, false, &a));
-    TRY(launch_ws_prepare(b, p, pd, dx, u->sumsq, a->xin, s));
+    TRY(get_acts(u, 1, pd.nz / f, pd.ny / f, pd.nx / f, false, &a));
+    const WsGrid g{pd.nx, pd.ny, pd.nz, pd.pitch, pd.plane, pd.plane + pd.pitch + 1};
+    const long long nc = a->nvox;
+    TRY(launch_ws_restrict(b, p, g, dx, f, a->ws, a->ws + nc, s));
+    TRY(launch_ws_prepare(a->ws, a->ws + nc, nc, (f * dx) * (f * dx), a->xin, a->ws + 2 * nc, s));
     TRY(forward(u, a, s));
-    TRY(launch_ws_apply(a->out, pd, dx, u->sumsq, p, s));
+    TRY(launch_ws_prolong(a->out, g, f, a->ws + 2 * nc, p, s));
     return GBSW_OK;
 }
 }  // namespace gbsw
@@ -351,8 +370,7 @@ gbsw_status unet_create(unsigned long long seed, void *stream, gbsw_unet **out)
     if (cudaMalloc((void **)&u->params, pb) != cudaSuccess || cudaMalloc((void **)&u->grads, pb) != cudaSuccess ||
         cudaMalloc((void **)&u->m, pb) != cudaSuccess || cudaMalloc((void **)&u->v, pb) != cudaSuccess ||
         cudaMalloc((void **)&u->status, sizeof(int)) != cudaSuccess ||
-        cudaMalloc((void **)&u->loss, sizeof(double)) != cudaSuccess ||
-        cudaMalloc((void **)&u->sumsq, sizeof(double)) != cudaSuccess)
+        cudaMalloc((void **)&u->loss, sizeof(double)) != cudaSuccess)
         return fail(GBSW_ERR_OOM);
     for (int l = 1; l < NLAYERS; ++l) {
         const size_t n = (size_t)27 * LAYERS[l].cin * LAYERS[l].cout * sizeof(bf16);
@@ -466,7 +484,6 @@ void unet_destroy(gbsw_unet *u)
     cudaFree(u->v);
     cudaFree(u->status);
     cudaFree(u->loss);
-    cudaFree(u->sumsq);
     delete u;
 }
 

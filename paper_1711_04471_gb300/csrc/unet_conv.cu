@@ -48,9 +48,10 @@ conv3d_tc_kernel(const __grid_constant__ CUtensorMap xmap, const __nv_bfloat16 *
     const int tx = t % g.tiles_x;
     t /= g.tiles_x;
     const int ty = t % g.tiles_y;
-    const int zn = t / g.tiles_y;
-    const int x0 = tx * g.box_x, y0 = ty * g.box_y;
-    const int z = zn % g.D;
+    const int tz = t / g.tiles_y;
+    const int x0 = tx * g.box_x, y0 = ty * g.box_y, z0 = tz * g.box_z;
+    const bool multi = g.box_z > 1;  // tile of several planes (small planes)
+    const int z = z0 % g.D;          // the plane of a single-plane tile
 
     if (warp == 0) {
         tc::tmem_alloc(tmem_slot, S::TMEM_COLS);
@@ -74,7 +75,7 @@ conv3d_tc_kernel(const __grid_constant__ CUtensorMap xmap, const __nv_bfloat16 *
         int it = 0;
         for (int tap = 0; tap < 27; ++tap) {
             const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-            if (z + dz < 0 || z + dz >= g.D) continue;
+            if (!multi && (z + dz < 0 || z + dz >= g.D)) continue;
             const int s = it % CONV_STAGES;
             if (it >= CONV_STAGES && !tc::mbar_wait(&empty[s], ((it / CONV_STAGES) - 1) & 1)) {
                 set_status(status, DEV_TIMEOUT);
@@ -82,7 +83,18 @@ conv3d_tc_kernel(const __grid_constant__ CUtensorMap xmap, const __nv_bfloat16 *
             }
             uint8_t *a = smem + s * S::STAGE;
             tc::mbar_arrive_expect_tx(&full[s], S::A_BYTES + S::B_BYTES);
-            tc::tma_load_5d(a, &xmap, &full[s], 0, x0 + dx, y0 + dy, 0, zn + dz);
+            if (!multi) {
+                tc::tma_load_5d(a, &xmap, &full[s], 0, x0 + dx, y0 + dy, 0, z0 + dz);
+            } else {
+                const int plane_bytes = g.box_x * g.box_y * 16;
+                for (int zz = 0; zz < g.box_z; ++zz) {
+                    const int zn = z0 + zz, zi = zn % g.D;
+                    const int zsrc = (zn < g.NZ && zi + dz >= 0 && zi + dz < g.D) ? zn + dz : -1;
+                    for (int cg = 0; cg < CIN / 8; ++cg)
+                        tc::tma_load_5d(a + cg * 2048 + zz * plane_bytes, &xmap, &full[s], 0, x0 + dx, y0 + dy, cg,
+                                        zsrc);
+                }
+            }
             tc::bulk_load(a + S::A_BYTES, wpack + (size_t)tap * COUT * CIN, S::B_BYTES, &full[s]);
             ++it;
         }
@@ -93,7 +105,7 @@ conv3d_tc_kernel(const __grid_constant__ CUtensorMap xmap, const __nv_bfloat16 *
         bool ok = true;
         for (int tap = 0; tap < 27 && ok; ++tap) {
             const int dz = tap / 9 - 1;
-            if (z + dz < 0 || z + dz >= g.D) continue;
+            if (!multi && (z + dz < 0 || z + dz >= g.D)) continue;
             const int s = it % CONV_STAGES;
             if (!tc::mbar_wait(&full[s], (it / CONV_STAGES) & 1)) {
                 set_status(status, DEV_TIMEOUT);
@@ -121,12 +133,15 @@ conv3d_tc_kernel(const __grid_constant__ CUtensorMap xmap, const __nv_bfloat16 *
     if (!ready && lane == 0) set_status(status, DEV_TIMEOUT);
     tc::fence_after_sync();
     const int m = warp * 32 + lane;
-    const int yy = y0 + m / g.box_x, xx = x0 + m % g.box_x;
+    const int plane = g.box_x * g.box_y;
+    const int zn = z0 + m / plane, r = m % plane;
+    const int yy = y0 + r / g.box_x, xx = x0 + r % g.box_x;
+    const bool stored = zn < g.NZ;  // false only past the last plane of a multi-plane tile
 #pragma unroll
     for (int cb = 0; cb < COUT / 8; ++cb) {
         float v[8];
         tc::tmem_ld8(tmem + ((uint32_t)(warp * 32) << 16) + cb * 8, v);
-        if (!ready) continue;
+        if (!ready || !stored) continue;
         if (epi == EPI_BIAS_RELU) {
 #pragma unroll
             for (int q = 0; q < 8; ++q) v[q] = fmaxf(v[q] + bias[cb * 8 + q], 0.0f);
@@ -239,7 +254,7 @@ gbsw_status launch_conv_t(const ConvCall &c, cudaStream_t s)
                                            S::BYTES));
         configured = true;
     }
-    const int ntiles = c.geom.NZ * c.geom.tiles_y * c.geom.tiles_x;
+    const int ntiles = c.geom.tiles_z * c.geom.tiles_y * c.geom.tiles_x;
     conv3d_tc_kernel<CIN, COUT><<<ntiles, CONV_THREADS, S::BYTES, s>>>(c.xmap, c.wpack, c.bias, c.y, c.y_f32, c.mask,
                                                                        c.geom, c.epi, c.status);
     GBSW_LAUNCH_CHECK();
@@ -254,16 +269,25 @@ gbsw_status conv_geometry(int NZ, int D, int H, int W, ConvGeom *g)
     if (NZ < 1 || D < 1 || NZ % D != 0 || H < 1 || W < 1) return GBSW_ERR_ARG;
     int bx = W >= 128 ? 128 : W;
     if (bx < 1 || 128 % bx != 0 || W % bx != 0) return GBSW_ERR_ARG;  // W a power of two or a multiple of 128
-    int by = 128 / bx;
-    if (H % by != 0) return GBSW_ERR_ARG;
+    int by = 128 / bx, bz = 1;
+    if (H < by) {
+        // small planes: the tile spans bz planes of H rows; boxes of >= 256 bytes
+        if (by % H != 0 || bx * H < 16) return GBSW_ERR_ARG;
+        bz = by / H;
+        by = H;
+    } else if (H % by != 0) {
+        return GBSW_ERR_ARG;
+    }
     g->NZ = NZ;
     g->D = D;
     g->H = H;
     g->W = W;
     g->box_x = bx;
     g->box_y = by;
+    g->box_z = bz;
     g->tiles_x = W / bx;
     g->tiles_y = H / by;
+    g->tiles_z = (NZ + bz - 1) / bz;
     g->out_cg_total = g->out_cg0 = g->mask_cg_total = g->mask_cg0 = 0;
     return GBSW_OK;
 }
@@ -277,7 +301,9 @@ gbsw_status conv_tensor_map(const __nv_bfloat16 *base, const ConvGeom &g, int cg
     const cuuint64_t dims[5] = {8, (cuuint64_t)g.W, (cuuint64_t)g.H, (cuuint64_t)cg_total, (cuuint64_t)g.NZ};
     const cuuint64_t strides[4] = {16, (cuuint64_t)g.W * 16, (cuuint64_t)g.H * g.W * 16,
                                    (cuuint64_t)cg_total * g.H * g.W * 16};
-    const cuuint32_t box[5] = {8, (cuuint32_t)g.box_x, (cuuint32_t)g.box_y, (cuuint32_t)cg_total, 1};
+    // one box per tap (all channel groups), or per (plane, group) for multi-plane tiles
+    const cuuint32_t box[5] = {8, (cuuint32_t)g.box_x, (cuuint32_t)g.box_y, g.box_z > 1 ? 1u : (cuuint32_t)cg_total,
+                               1};
     const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
     CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, (void *)base, dims, strides, box, estr,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,

@@ -14,7 +14,15 @@
 // Weights per tap are packed as [ci/8][co][8] BF16 (the same canonical
 // layout with N = Cout rows), copied per tap with one bulk copy.
 //
-// One CTA computes one tile of 128 voxels (box_y rows of box_x voxels) and
+// Small planes (box_x * H < 128, the coarse levels of a network run on a
+// coarsened grid) make a tile of box_z consecutive planes of box_y = H rows.
+// Each (plane, channel group) is then one TMA box {8, box_x, box_y, 1, 1}
+// placed at plane * box_x * box_y * 16 bytes inside its slab, which keeps the
+// canonical layout; a plane whose tap leaves its sample, or that lies past
+// the last plane, is loaded from z = -1 (all out of bounds: zero fill) and
+// its voxels are not stored.
+//
+// One CTA computes one tile of 128 voxels (box_z x box_y x box_x) and
 // all Cout channels: thread 0 of warp 0 issues the loads of tap t into a
 // 4-stage ring, thread 0 of warp 1 issues Cin/16 MMAs (M=128, N=Cout, K=16)
 // per tap and commits each stage back to the producer, and all four warps
@@ -30,8 +38,9 @@ namespace gbsw {
 struct ConvGeom {
     int NZ, H, W;        // samples*D, rows, columns
     int D;               // depth of one sample
-    int box_x, box_y;    // tile = box_y rows x box_x voxels (box_x*box_y = 128)
-    int tiles_x, tiles_y;
+    int box_x, box_y;    // tile = box_z planes x box_y rows x box_x voxels = 128 voxels
+    int box_z;           // 1 unless box_x * H < 128
+    int tiles_x, tiles_y, tiles_z;
     int out_cg_total, out_cg0;    // output tensor channel groups and offset
     int mask_cg_total, mask_cg0;  // mask tensor (EPI_MASK)
 };

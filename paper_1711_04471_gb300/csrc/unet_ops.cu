@@ -1,6 +1,6 @@
 // U-Net glue kernels: the first (2-channel) convolution on CUDA cores,
 // pooling / upsampling in the C8-blocked layout, the 1x1 head with the MSE
-// loss, weight gradients, Adam, and the warm-start input/output transforms.
+// loss, weight gradients and Adam.
 #include <algorithm>
 
 #include "unet_ops.cuh"
@@ -136,7 +136,8 @@ wgrad_kernel(const __nv_bfloat16 *__restrict__ x, int x_cg_total, int x_cg0, con
     __shared__ float sx[64][CIN + 1];
     const int tap = blockIdx.x;
     const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-    const int ntiles = geo.NZ * geo.tiles_y * geo.tiles_x;
+    const int ntiles = geo.tiles_z * geo.tiles_y * geo.tiles_x;
+    const int plane = geo.box_x * geo.box_y;  // voxels of one plane of a tile
     float acc[PER];
 #pragma unroll
     for (int q = 0; q < PER; ++q) acc[q] = 0.0f;
@@ -146,25 +147,28 @@ wgrad_kernel(const __nv_bfloat16 *__restrict__ x, int x_cg_total, int x_cg0, con
         const int tx = tt % geo.tiles_x;
         tt /= geo.tiles_x;
         const int ty = tt % geo.tiles_y;
-        const int zn = tt / geo.tiles_y;
-        const int z = zn % geo.D;
+        const int z0 = (tt / geo.tiles_y) * geo.box_z;
         const int x0 = tx * geo.box_x, y0 = ty * geo.box_y;
         for (int half = 0; half < 2; ++half) {
             __syncthreads();
             // stage 64 voxels: one thread per (voxel, channel group)
             for (int q = threadIdx.x; q < 64 * (COUT / 8); q += 256) {
                 const int mm = q % 64, cb = q / 64, m = half * 64 + mm;
-                const int yy = y0 + m / geo.box_x, xx = x0 + m % geo.box_x;
-                const uint4 pk =
-                    *reinterpret_cast<const uint4 *>(g + bidx(zn, g_cg_total, g_cg0 + cb, geo.H, geo.W, yy, xx));
+                const int zn = z0 + m / plane, r = m % plane;
+                const int yy = y0 + r / geo.box_x, xx = x0 + r % geo.box_x;
+                uint4 pk = make_uint4(0, 0, 0, 0);  // voxels past the last plane contribute nothing
+                if (zn < geo.NZ)
+                    pk = *reinterpret_cast<const uint4 *>(g + bidx(zn, g_cg_total, g_cg0 + cb, geo.H, geo.W, yy, xx));
                 const __nv_bfloat16 *pb = reinterpret_cast<const __nv_bfloat16 *>(&pk);
 #pragma unroll
                 for (int k = 0; k < 8; ++k) sg[mm][cb * 8 + k] = __bfloat162float(pb[k]);
             }
             for (int q = threadIdx.x; q < 64 * (CIN / 8); q += 256) {
                 const int mm = q % 64, cb = q / 64, m = half * 64 + mm;
-                const int yy = y0 + m / geo.box_x + dy, xx = x0 + m % geo.box_x + dx;
-                const bool in = z + dz >= 0 && z + dz < geo.D && yy >= 0 && yy < geo.H && xx >= 0 && xx < geo.W;
+                const int zn = z0 + m / plane, r = m % plane, z = zn % geo.D;
+                const int yy = y0 + r / geo.box_x + dy, xx = x0 + r % geo.box_x + dx;
+                const bool in = zn < geo.NZ && z + dz >= 0 && z + dz < geo.D && yy >= 0 && yy < geo.H && xx >= 0 &&
+                                xx < geo.W;
                 uint4 pk = make_uint4(0, 0, 0, 0);
                 if (in)
                     pk = *reinterpret_cast<const uint4 *>(
@@ -404,64 +408,6 @@ __global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g, 
     p[q] -= lr * (mq / c1) / (sqrtf(vq / c2) + eps);
 }
 
-// ------------------------------------------------- warm start in / out
-// Sum of squares of b over the interior of an LES padded field (FP64).
-__global__ void __launch_bounds__(256)
-ws_sumsq_kernel(const float *__restrict__ b, PadDims pd, double *__restrict__ out)
-{
-    __shared__ double red[8];
-    double s = 0.0;
-    const long long n = (long long)pd.nx * pd.ny * pd.nz;
-    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(q % pd.nx) + 1;
-        const int j = (int)((q / pd.nx) % pd.ny) + 1;
-        const int k = (int)(q / ((long long)pd.nx * pd.ny)) + 1;
-        const double v = b[(long long)k * pd.plane + (long long)j * pd.pitch + i];
-        s += v * v;
-    }
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int k = 0; k < 8; ++k) t += red[k];
-        atomicAdd(out, t);
-    }
-}
-
-// Network input [b dx^2 / s, p_prev / s] (dense FP32, 2 channels) from the
-// LES fields; s = dx^2 * rms(b) is read from sumsq on the device.
-__global__ void ws_prepare_kernel(const float *__restrict__ b, const double *__restrict__ p, PadDims pd, double dx2,
-                                  const double *__restrict__ sumsq, float *__restrict__ xin)
-{
-    const long long n = (long long)pd.nx * pd.ny * pd.nz;
-    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= n) return;
-    const double rms = sqrt(*sumsq / (double)n);
-    const double s = rms > 0.0 ? dx2 * rms : 1.0;
-    const int i = (int)(q % pd.nx) + 1;
-    const int j = (int)((q / pd.nx) % pd.ny) + 1;
-    const int k = (int)(q / ((long long)pd.nx * pd.ny)) + 1;
-    const long long c = (long long)k * pd.plane + (long long)j * pd.pitch + i;
-    xin[2 * q] = (float)(b[c] * dx2 / s);
-    xin[2 * q + 1] = (float)(p[c] / s);
-}
-
-// p += s * out (the predicted increment), interior cells.
-__global__ void ws_apply_kernel(const float *__restrict__ out, PadDims pd, double dx2, const double *__restrict__ sumsq,
-                                double *__restrict__ p)
-{
-    const long long n = (long long)pd.nx * pd.ny * pd.nz;
-    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= n) return;
-    const double rms = sqrt(*sumsq / (double)n);
-    const double s = rms > 0.0 ? dx2 * rms : 1.0;
-    const int i = (int)(q % pd.nx) + 1;
-    const int j = (int)((q / pd.nx) % pd.ny) + 1;
-    const int k = (int)(q / ((long long)pd.nx * pd.ny)) + 1;
-    p[(long long)k * pd.plane + (long long)j * pd.pitch + i] += s * (double)out[q];
-}
-
 }  // namespace gbsw
 
 // ----------------------------------------------------------------- launches
@@ -493,7 +439,7 @@ gbsw_status launch_wgrad_in2(const float *x, const bf16 *g, int g_cg_total, int 
 gbsw_status launch_wgrad(int cin, int cout, const bf16 *x, int x_cg_total, int x_cg0, const bf16 *g, int g_cg_total,
                          int g_cg0, const ConvGeom &geo, float *dw, float *db, cudaStream_t s)
 {
-    const int ntiles = geo.NZ * geo.tiles_y * geo.tiles_x;
+    const int ntiles = geo.tiles_z * geo.tiles_y * geo.tiles_x;
     const int chunks = std::max(1, std::min(ntiles, 4 * sm_count() / 27 + 1));
     const int per = ceil_div(ntiles, chunks);
     const dim3 grid(27, ceil_div(ntiles, per));
@@ -575,26 +521,6 @@ gbsw_status launch_adam(float *p, const float *g, float *m, float *v, int n, flo
     const float b1 = 0.9f, b2 = 0.999f;
     const float c1 = 1.0f - powf(b1, (float)step), c2 = 1.0f - powf(b2, (float)step);
     adam_kernel<<<nblk(n, 256), 256, 0, s>>>(p, g, m, v, n, lr, b1, b2, 1e-8f, c1, c2);
-    GBSW_LAUNCH_CHECK();
-    return GBSW_OK;
-}
-
-gbsw_status launch_ws_prepare(const float *b, const double *p, const PadDims &pd, double dx, double *sumsq,
-                              float *xin, cudaStream_t s)
-{
-    const long long n = (long long)pd.nx * pd.ny * pd.nz;
-    GBSW_CUDA_TRY(cudaMemsetAsync(sumsq, 0, sizeof(double), s));
-    ws_sumsq_kernel<<<(unsigned)std::min<long long>(4LL * sm_count(), nblk(n, 256)), 256, 0, s>>>(b, pd, sumsq);
-    ws_prepare_kernel<<<nblk(n, 256), 256, 0, s>>>(b, p, pd, dx * dx, sumsq, xin);
-    GBSW_LAUNCH_CHECK();
-    return GBSW_OK;
-}
-
-gbsw_status launch_ws_apply(const float *out, const PadDims &pd, double dx, const double *sumsq, double *p,
-                            cudaStream_t s)
-{
-    const long long n = (long long)pd.nx * pd.ny * pd.nz;
-    ws_apply_kernel<<<nblk(n, 256), 256, 0, s>>>(out, pd, dx * dx, sumsq, p);
     GBSW_LAUNCH_CHECK();
     return GBSW_OK;
 }

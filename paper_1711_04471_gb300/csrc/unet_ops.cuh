@@ -37,13 +37,14 @@ gbsw_status launch_head_bwd(const bf16 *d1, int cg_total, int cg0, long long nvo
                             const float *target, const float *hw, float *g_hw, float *g_hb, bf16 *g_d1, double *loss,
                             cudaStream_t s);
 gbsw_status launch_adam(float *p, const float *g, float *m, float *v, int n, float lr, int step, cudaStream_t s);
-gbsw_status launch_ws_prepare(const float *b, const double *p, const PadDims &pd, double dx, double *sumsq,
-                              float *xin, cudaStream_t s);
-gbsw_status launch_ws_apply(const float *out, const PadDims &pd, double dx, const double *sumsq, double *p,
-                            cudaStream_t s);
+// True if a (1, D, H, W) input fits the network: D, H, W multiples of 4 and
+// every level within the tile geometry of the tcgen05 convolution.
+bool unet_shape_ok(int D, int H, int W);
 
 // LES hook: p += the network's pressure increment for right-hand side b
-// and previous pressure p (padded LES layout), on stream s.
-gbsw_status unet_warm_start(gbsw_unet *u, const float *b, double *p, const PadDims &pd, double dx, cudaStream_t s);
+// and previous pressure p (padded LES layout), the network run on the grid
+// coarsened by f (warmstart.cu), on stream s.
+gbsw_status unet_warm_start(gbsw_unet *u, const float *b, double *p, const PadDims &pd, double dx, int f,
+                            cudaStream_t s);
 
 }  // namespace gbsw

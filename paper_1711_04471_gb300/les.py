@@ -72,10 +72,12 @@ class LES:
         p.check_every = p.check_every if check_every is None else int(check_every)
         N.check(N.lib().les_set_solver(self._h, p.omega, p.tol, p.max_iter, p.check_every), "les_set_solver")
 
-    def set_warm_start(self, net):
+    def set_warm_start(self, net, factor: int = 0):
         """Use a UNet (paper_1711_04471_gb300.unet.UNet) as the pressure warm
-        start, or None for the previous pressure.  The network must outlive
-        its use here."""
+        start, run on the grid coarsened by `factor` (0: the default, 16 on
+        a 256 x 256 x 128 grid), or None for the previous pressure.  The
+        network must outlive its use here."""
+        N.check(N.lib().les_set_warm_start_factor(self._h, int(factor)), "les_set_warm_start_factor")
         self._net = net
         N.check(N.lib().les_set_warm_start(self._h, None if net is None else net._h), "les_set_warm_start")
 
@@ -111,3 +113,27 @@ def poisson_solve(p, b, dx: float, omega=1.8, tol=1e-6, max_iter=100000, check_e
                                int(max_iter), int(check_every), N.stream_handle(stream), C.byref(it), C.byref(rr))
     N.check(st, "poisson_solve")
     return st, it.value, rr.value
+
+
+def warm_start_features(p, b, dx: float, f: int, stream=None):
+    """Network input of the warm start from CUDA tensors p (float64) and b
+    (float32) of shape (nz, ny, nx).  Returns (x, s): x a CUDA float32
+    tensor (nz/f, ny/f, nx/f, 2), s the scale of the network's output."""
+    import torch
+    nz, ny, nx = p.shape
+    assert b.shape == p.shape
+    x = torch.empty((nz // f, ny // f, nx // f, 2), dtype=torch.float32, device=p.device)
+    s = C.c_double()
+    N.check(N.lib().warm_start_features(nx, ny, nz, dx, int(f), N.tensor_ptr(p, "float64"), N.tensor_ptr(b, "float32"),
+                                        N.tensor_ptr(x, "float32"), C.byref(s), N.stream_handle(stream)),
+            "warm_start_features")
+    return x, s.value
+
+
+def warm_start_apply(out, scale: float, p, f: int, stream=None):
+    """p += scale * prolong(out) in place; out CUDA float32 (nz/f, ny/f, nx/f),
+    p CUDA float64 (nz, ny, nx)."""
+    nz, ny, nx = p.shape
+    assert tuple(out.shape) == (nz // f, ny // f, nx // f)
+    N.check(N.lib().warm_start_apply(nx, ny, nz, int(f), N.tensor_ptr(out, "float32"), float(scale),
+                                     N.tensor_ptr(p, "float64"), N.stream_handle(stream)), "warm_start_apply")

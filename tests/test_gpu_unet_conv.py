@@ -52,7 +52,12 @@ def rel(a, b):
 
 @pytest.mark.parametrize("shape,cin,cout", [((2, 4, 8, 16), 16, 16), ((1, 3, 4, 32), 16, 32), ((1, 2, 2, 128), 32, 64),
                                             ((1, 2, 1, 256), 64, 32), ((2, 5, 8, 16), 64, 16), ((1, 4, 4, 32), 32, 16),
-                                            ((1, 3, 8, 16), 16, 64), ((1, 2, 4, 32), 32, 32)])
+                                            ((1, 3, 8, 16), 16, 64), ((1, 2, 4, 32), 32, 32),
+                                            # small planes: tiles of several planes, partial last tiles,
+                                            # tiles that cross from one sample into the next
+                                            ((3, 2, 4, 4), 32, 64), ((3, 2, 4, 4), 64, 32), ((2, 3, 8, 8), 16, 32),
+                                            ((1, 4, 8, 8), 64, 16), ((1, 2, 4, 4), 32, 32), ((2, 4, 4, 8), 32, 16),
+                                            ((5, 2, 4, 4), 16, 16)])
 def test_conv_forward_bias_relu(conv, shape, cin, cout):
     rng = np.random.default_rng(cin * 100 + cout)
     n, D, H, W = shape
@@ -86,3 +91,16 @@ def test_conv_sample_boundary_in_z(conv):
     w = bf16(rng.standard_normal((27, 16, 16)))
     y = conv(x, w, np.zeros(16, np.float32), 1)
     assert not np.any(y[0])
+
+
+def test_conv_epilogues_on_multi_plane_tiles(conv):
+    rng = np.random.default_rng(4)
+    x = bf16(rng.standard_normal((3, 2, 4, 4, 64)))
+    w = bf16(rng.standard_normal((27, 32, 64)) * 0.2)
+    b = np.zeros(32, np.float32)
+    raw = np.stack([U.conv3d(x[k].astype(np.float64), w.astype(np.float64)) for k in range(3)])
+    assert rel(conv(x, w, b, 1), raw) <= 1e-5
+    mask = bf16(rng.standard_normal((3, 2, 4, 4, 32)))
+    got = conv(x, w, b, 2, mask)
+    assert rel(got, raw * (mask > 0)) <= 1e-5
+    assert np.all(got[mask <= 0] == 0)
