@@ -11,12 +11,19 @@ whole domain, so the warm start runs it on a grid coarsened by a factor f in
 each direction:
 
     r      = b - A p_prev                       (fine residual of the previous pressure)
-    r_c    = block mean of r over f^3 cells     (restriction)
-    p_c    = block mean of p_prev
+    r_c    = prolong^T r / f^3                  (full-weighting restriction)
+    p_c    = prolong^T p_prev / f^3
     s      = (f dx)^2 rms(r_c)                  (scale of the coarse increment)
     x      = [r_c / rms(r_c), p_c / rms(p_c)]   (network input, 2 channels)
     target = block mean of (p - p_prev) / s     (p the converged pressure)
     guess  = p_prev + s * prolong(out)          (out the network's output)
+
+The input is restricted with the adjoint of the prolongation (the
+restriction of Galerkin coarse-grid correction), which keeps the inner
+product of r with every prolongated coarse field: the projection of r on the
+slowest mode, which sets that mode's amplitude in p - p_prev, is kept to
+second order, where block means lose the variation of the mode inside a
+block.
 
 prolong is trilinear interpolation between coarse cell centres: fine cell i
 (0-based) sits at coarse coordinate (i + 1/2)/f - 1/2.  Beyond the end
@@ -68,13 +75,25 @@ def _axis_weights(n: int, nc: int, f: int, rule: str) -> np.ndarray:
     return M
 
 
+def _weights(nz: int, ny: int, nx: int, f: int):
+    return (_axis_weights(nz, nz // f, f, "neumann"), _axis_weights(ny, ny // f, f, "periodic"),
+            _axis_weights(nx, nx // f, f, "outflow"))
+
+
 def prolong(c: np.ndarray, f: int) -> np.ndarray:
     """Trilinear interpolation of a coarse (ncz, ncy, ncx) field to the fine grid."""
     ncz, ncy, ncx = c.shape
-    Wz = _axis_weights(ncz * f, ncz, f, "neumann")
-    Wy = _axis_weights(ncy * f, ncy, f, "periodic")
-    Wx = _axis_weights(ncx * f, ncx, f, "outflow")
+    Wz, Wy, Wx = _weights(ncz * f, ncy * f, ncx * f, f)
     return np.einsum("zk,yj,xi,kji->zyx", Wz, Wy, Wx, c)
+
+
+def restrict_fw(a: np.ndarray, f: int) -> np.ndarray:
+    """Full weighting: prolong^T a / f^3 for a fine (nz, ny, nx) field."""
+    nz, ny, nx = a.shape
+    if nz % f or ny % f or nx % f:
+        raise ValueError("grid not divisible by f")
+    Wz, Wy, Wx = _weights(nz, ny, nx, f)
+    return np.einsum("zk,yj,xi,zyx->kji", Wz, Wy, Wx, a) / f ** 3
 
 
 def residual_field(P, b: np.ndarray, p: np.ndarray) -> np.ndarray:
@@ -85,8 +104,8 @@ def residual_field(P, b: np.ndarray, p: np.ndarray) -> np.ndarray:
 def features(P, b: np.ndarray, p_prev: np.ndarray, f: int):
     """Network input (ncz, ncy, ncx, 2) and scale s from padded b and p_prev."""
     r = residual_field(P, np.ascontiguousarray(b, dtype=np.float64), p_prev)
-    rc = restrict(r, f)
-    pc = restrict(ol.interior(p_prev), f)
+    rc = restrict_fw(r, f)
+    pc = restrict_fw(np.asarray(ol.interior(p_prev), dtype=np.float64), f)
     rms_r = math.sqrt(float(np.mean(rc * rc)))
     rms_p = math.sqrt(float(np.mean(pc * pc)))
     x = np.stack([rc / rms_r if rms_r > 0 else np.zeros_like(rc), pc / rms_p if rms_p > 0 else np.zeros_like(pc)],

@@ -1,8 +1,9 @@
 """Pins of the warm start's grid transfers in the oracle (oracle/warmstart.py):
 brute-force block means, a library trilinear interpolation, exactness on
-linear fields, the telescoping identity of the Poisson residual, scale
-covariance and second-order accuracy of restrict-then-prolong on the
-slowest SOR mode."""
+linear fields, full weighting as the column-by-column adjoint of the
+prolongation, the telescoping identity of the Poisson residual, scale
+covariance, second-order accuracy of restrict-then-prolong on the slowest
+SOR mode and of the full-weighted projection on it."""
 import math
 
 import numpy as np
@@ -95,6 +96,41 @@ def test_residual_sum_telescopes_to_the_outflow_column():
     assert ws.restrict(r, f).sum() * f ** 3 == pytest.approx(want, rel=1e-12, abs=1e-12)
 
 
+def test_full_weighting_is_the_adjoint_of_prolong():
+    """Column by column: restrict_fw(a)[I] = <prolong(e_I), a> / f^3, with e_I
+    the coarse unit fields; hence <prolong(c), a> = f^3 <c, restrict_fw(a)>."""
+    f, shape_c = 2, (2, 3, 4)
+    a = _rng(6).standard_normal(tuple(n * f for n in shape_c))
+    got = ws.restrict_fw(a, f)
+    for idx in np.ndindex(shape_c):
+        e = np.zeros(shape_c)
+        e[idx] = 1.0
+        assert got[idx] == pytest.approx(np.sum(ws.prolong(e, f) * a) / f ** 3, rel=1e-12, abs=1e-14)
+    c = _rng(7).standard_normal(shape_c)
+    assert np.sum(ws.prolong(c, f) * a) == pytest.approx(f ** 3 * np.sum(c * got), rel=1e-12)
+    assert np.allclose(ws.restrict_fw(a, 1), a, rtol=0, atol=1e-15)
+
+
+def test_full_weighting_keeps_the_slow_mode_projection():
+    """<phi, r> for the slowest mode phi and a rough r: full weighting keeps it
+    to O((f/nx)^2) of |phi| |r|; block means make an O(f/nx) error."""
+    nx, ny, nz, f = 128, 8, 8, 8
+    x = np.arange(nx) + 0.5
+    phi = np.broadcast_to(np.cos(np.pi * x / (2 * nx))[None, None, :], (nz, ny, nx))
+    phic = np.cos(np.pi * (np.arange(nx // f) + 0.5) * f / (2 * nx))
+    worst_fw, worst_bm = 0.0, 0.0
+    for seed in range(5):
+        r = _rng(10 + seed).standard_normal((nz, ny, nx))
+        exact = np.sum(phi * r)
+        fw = f ** 3 * np.sum(phic[None, None, :] * ws.restrict_fw(r, f))
+        bm = f ** 3 * np.sum(phic[None, None, :] * ws.restrict(r, f))
+        scale = np.linalg.norm(phi) * np.linalg.norm(r)
+        worst_fw = max(worst_fw, abs(fw - exact) / scale)
+        worst_bm = max(worst_bm, abs(bm - exact) / scale)
+    assert worst_fw < 3e-3
+    assert worst_bm > 3 * worst_fw
+
+
 def test_features_scale_with_the_fields():
     nx, ny, nz, dx, f = 8, 8, 4, 2.0, 2
     P = ol.make_params(nx, ny, nz, dx=dx)
@@ -106,7 +142,7 @@ def test_features_scale_with_the_fields():
     x2, s2 = ws.features(P, 3.0 * b, 3.0 * p, f)
     assert np.allclose(x1, x2, rtol=1e-12, atol=1e-12)
     assert s2 == pytest.approx(3.0 * s1, rel=1e-12)
-    rc = ws.restrict(ws.residual_field(P, b, p), f)
+    rc = ws.restrict_fw(ws.residual_field(P, b, p), f)
     assert s1 == pytest.approx((f * dx) ** 2 * math.sqrt(np.mean(rc ** 2)), rel=1e-12)
     assert np.mean(x1[..., 0] ** 2) == pytest.approx(1.0, rel=1e-12)
     assert np.mean(x1[..., 1] ** 2) == pytest.approx(1.0, rel=1e-12)
