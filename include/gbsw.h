@@ -378,10 +378,12 @@ gbsw_status les_set_warm_start_factor(gbsw_les *les, int f);
  *   p      device, nz*ny*nx FP64, the previous pressure (dense, x fastest)
  *   b      device, nz*ny*nx FP32, the right-hand side (divergence / dt)
  *   x      device, out: (nz/f)(ny/f)(nx/f) x 2 FP32, channels last:
- *          [r_c / rms(r_c), p_c / rms(p_c)], r_c and p_c the block means over
- *          f^3 cells of r = b - A p and of p (A: the operator of poisson_solve)
+ *          [r_c / rms(r_c), p_c / rms(p_c)], r_c and p_c the full-weighted
+ *          restrictions (the adjoint of warm_start_apply's prolongation,
+ *          divided by f^3) of r = b - A p and of p (A: the operator of
+ *          poisson_solve)
  *   scale  host, out: s = (f dx)^2 rms(r_c), the unit of the network's output
- * f a power of two dividing nx, ny, nz.  Block sums in FP64, fixed order.
+ * f a power of two dividing nx, ny, nz.  Sums in FP64, fixed order.
  * Synchronous.  The training target for a converged pressure p_new is the
  * block mean of (p_new - p) / s.
  */

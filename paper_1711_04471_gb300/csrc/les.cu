@@ -295,6 +295,8 @@ struct gbsw_les {
     int fixed_iters;       // > 0: paper mode, exactly this many SOR iterations per step
     gbsw_unet *net;        // learned warm start (not owned), NULL = previous pressure
     int ws_factor;         // the network runs on the grid coarsened by this factor (0 = default)
+    double *ws_scratch;    // restriction passes of the warm start
+    size_t ws_scratch_n;
     size_t n;              // elements per padded field
 };
 
@@ -495,7 +497,20 @@ gbsw_status les_step(gbsw_les *s, int nsteps, gbsw_les_stats *stats)
         if (st != GBSW_OK) break;
         if (stats) cudaEventRecord(ev[4 * t + 1], s->stream);
         if (s->net) {
-            st = unet_warm_start(s->net, s->b, s->solver.p_hi, pd, s->p.dx, ws_factor_of(s), s->stream);
+            const int f = ws_factor_of(s);
+            const size_t need = ws_scratch_doubles(pd.nx, pd.ny, pd.nz, f);
+            if (need > s->ws_scratch_n) {
+                cudaStreamSynchronize(s->stream);
+                cudaFree(s->ws_scratch);
+                s->ws_scratch_n = 0;
+                if (cudaMalloc((void **)&s->ws_scratch, need * sizeof(double)) != cudaSuccess) {
+                    s->ws_scratch = nullptr;
+                    st = GBSW_ERR_OOM;
+                    break;
+                }
+                s->ws_scratch_n = need;
+            }
+            st = unet_warm_start(s->net, s->b, s->solver.p_hi, pd, s->p.dx, f, s->ws_scratch, s->stream);
             if (st != GBSW_OK) break;
         }
         if (stats) cudaEventRecord(ev[4 * t + 2], s->stream);
@@ -632,6 +647,7 @@ void les_destroy(gbsw_les *s)
     for (float *x : fl) cudaFree(x);
     cudaFree(s->face);
     cudaFree(s->ctl_log);
+    cudaFree(s->ws_scratch);
     s->solver.release();
     delete s;
 }

@@ -320,14 +320,14 @@ bool unet_shape_ok(int D, int H, int W)
 }
 
 gbsw_status unet_warm_start(gbsw_unet *u, const float *b, double *p, const PadDims &pd, double dx, int f,
-                            cudaStream_t s)
+                            double *scratch, cudaStream_t s)
 {
     if (!ws_factor_ok(pd.nx, pd.ny, pd.nz, f)) return GBSW_ERR_ARG;
     Acts *a = nullptr;
     TRY(get_acts(u, 1, pd.nz / f, pd.ny / f, pd.nx / f, false, &a));
     const WsGrid g{pd.nx, pd.ny, pd.nz, pd.pitch, pd.plane, pd.plane + pd.pitch + 1};
     const long long nc = a->nvox;
-    TRY(launch_ws_restrict(b, p, g, dx, f, a->ws, a->ws + nc, s));
+    TRY(launch_ws_restrict(b, p, g, dx, f, scratch, a->ws, a->ws + nc, s));
     TRY(launch_ws_prepare(a->ws, a->ws + nc, nc, (f * dx) * (f * dx), a->xin, a->ws + 2 * nc, s));
     TRY(forward(u, a, s));
     TRY(launch_ws_prolong(a->out, g, f, a->ws + 2 * nc, p, s));

@@ -43,8 +43,9 @@ bool unet_shape_ok(int D, int H, int W);
 
 // LES hook: p += the network's pressure increment for right-hand side b
 // and previous pressure p (padded LES layout), the network run on the grid
-// coarsened by f (warmstart.cu), on stream s.
+// coarsened by f (warmstart.cu), on stream s.  scratch: device, at least
+// ws_scratch_doubles(nx, ny, nz, f) doubles.
 gbsw_status unet_warm_start(gbsw_unet *u, const float *b, double *p, const PadDims &pd, double dx, int f,
-                            cudaStream_t s);
+                            double *scratch, cudaStream_t s);
 
 }  // namespace gbsw

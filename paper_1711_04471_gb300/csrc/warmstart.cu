@@ -3,7 +3,7 @@
 // receptive field spans the domain and reaches the smooth error modes that
 // set the SOR iteration count):
 //
-//   r_c = block mean over f^3 cells of r = b - A p_prev,  p_c = block mean of p_prev
+//   r_c = prolong^T r / f^3 for r = b - A p_prev,  p_c = prolong^T p_prev / f^3
 //   x   = [r_c / rms(r_c), p_c / rms(p_c)]   (network input, FP32, 2 channels)
 //   s   = (f dx)^2 rms(r_c)
 //   p  += s * prolong(out)                  (out: the network's coarse output)
@@ -13,7 +13,10 @@
 // trilinearly between coarse cell centres (fine cell i at coarse coordinate
 // (i + 1/2)/f - 1/2); beyond the end centres it holds the end value at the
 // Neumann walls, takes minus the last value as the ghost past the outflow
-// and wraps in y.  Block sums run in FP64 in a fixed order (deterministic).
+// and wraps in y.  The restriction (full weighting, the prolongation's
+// adjoint) keeps the residual's projection on the slowest mode, which sets
+// that mode's amplitude in the increment; it runs as three separable passes
+// in FP64, each sum in a fixed order (deterministic).
 #include "warmstart.cuh"
 
 namespace gbsw {
@@ -28,52 +31,111 @@ __device__ __forceinline__ long long ws_at(const WsGrid &g, int i, int j, int k)
     return g.off + (long long)(k - 1) * g.sz + (long long)(j - 1) * g.sy + (i - 1);
 }
 
-// One group of tpc = min(f^3, 256) threads per coarse cell; the group's
-// partial sums meet in a shared-memory tree (fixed order).
-__global__ void __launch_bounds__(WS_THREADS)
-ws_restrict_kernel(const float *__restrict__ b, const double *__restrict__ p, WsGrid g, double dx, int f,
-                   double *__restrict__ rc, double *__restrict__ pc)
+// Weight of coarse index I in the interpolation at fine index i along one
+// axis (the prolongation's rule): 0 = end values held (Neumann walls),
+// 1 = periodic, 2 = held at the start, antisymmetric ghost past the end
+// (outflow).  Full weighting applies the same weights transposed.
+__device__ __forceinline__ double ws_weight(int i, int I, int nc, double inv, int rule)
 {
-    __shared__ double sr[WS_THREADS], sp[WS_THREADS];
-    const int f3 = f * f * f;
-    const int tpc = f3 < WS_THREADS ? f3 : WS_THREADS;
-    const int ncx = g.nx / f, ncy = g.ny / f, ncz = g.nz / f;
-    const long long nc = (long long)ncx * ncy * ncz;
-    const long long q = (long long)blockIdx.x * (WS_THREADS / tpc) + threadIdx.x / tpc;
-    const int lane = threadIdx.x % tpc;
-    const double r2 = 1.0 / (dx * dx);
-    double accr = 0.0, accp = 0.0;
-    if (q < nc) {
-        const int I = (int)(q % ncx), J = (int)((q / ncx) % ncy), K = (int)(q / ((long long)ncx * ncy));
-        auto P = [&](int i, int j, int k) -> double {
-            if (i < 1 || i > g.nx || k < 1 || k > g.nz) return 0.0;
-            return p[ws_at(g, i, j, k)];
-        };
-        for (int t = lane; t < f3; t += tpc) {
-            const int i = I * f + t % f + 1, j = J * f + (t / f) % f + 1, k = K * f + t / (f * f) + 1;
-            const int jm = j == 1 ? g.ny : j - 1, jp = j == g.ny ? 1 : j + 1;
-            const double diag = 6.0 - (i == 1) - (k == 1) - (k == g.nz) + (i == g.nx);
-            const double pv = P(i, j, k);
-            const double nb = (P(i - 1, j, k) + P(i + 1, j, k)) + (P(i, jm, k) + P(i, jp, k)) +
-                              (P(i, j, k - 1) + P(i, j, k + 1));
-            accr += (double)b[ws_at(g, i, j, k)] - (nb - diag * pv) * r2;
-            accp += pv;
-        }
+    double X = (i + 0.5) * inv - 0.5;
+    if (rule == 1) {
+        const int i0 = (int)floor(X);
+        const double w = X - i0;
+        const int c0 = ((i0 % nc) + nc) % nc, c1 = (c0 + 1) % nc;
+        return (c0 == I ? 1.0 - w : 0.0) + (c1 == I ? w : 0.0);
     }
-    sr[threadIdx.x] = accr;
-    sp[threadIdx.x] = accp;
-    __syncthreads();
-    for (int h = tpc / 2; h > 0; h >>= 1) {
-        if (lane < h) {
-            sr[threadIdx.x] += sr[threadIdx.x + h];
-            sp[threadIdx.x] += sp[threadIdx.x + h];
-        }
-        __syncthreads();
+    X = fmax(X, 0.0);
+    if (rule == 0) X = fmin(X, nc - 1.0);
+    const int i0 = min((int)floor(X), nc - 1);
+    const double w = X - i0;
+    if (i0 + 1 < nc) return (i0 == I ? 1.0 - w : 0.0) + (i0 + 1 == I ? w : 0.0);
+    return I == nc - 1 ? (rule == 2 ? 1.0 - 2.0 * w : 1.0) : 0.0;
+}
+
+// Full weighting, pass x: ar/ap (nz, ny, ncx) = weighted sums along x of
+// r = b - A p (formed here) and of p.  Coarse I draws on the 2f fine cells
+// [I f - f/2, I f + 3f/2) (clipped); the sums run in a fixed order.
+__global__ void __launch_bounds__(WS_THREADS)
+ws_fw_x_kernel(const float *__restrict__ b, const double *__restrict__ p, WsGrid g, double dx, int f,
+               double *__restrict__ ar, double *__restrict__ ap)
+{
+    const int ncx = g.nx / f;
+    const long long n = (long long)g.nz * g.ny * ncx;
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const int I = (int)(q % ncx);
+    const int j = (int)((q / ncx) % g.ny) + 1;
+    const int k = (int)(q / ((long long)ncx * g.ny)) + 1;
+    const int jm = j == 1 ? g.ny : j - 1, jp = j == g.ny ? 1 : j + 1;
+    const double r2 = 1.0 / (dx * dx), inv = 1.0 / f;
+    auto P = [&](int ii, int jj, int kk) -> double {
+        if (ii < 1 || ii > g.nx || kk < 1 || kk > g.nz) return 0.0;
+        return p[ws_at(g, ii, jj, kk)];
+    };
+    double sr = 0.0, sp = 0.0;
+    const int lo = max(I * f - f / 2, 0), hi = min(I * f + (3 * f) / 2, g.nx);
+    for (int i0 = lo; i0 < hi; ++i0) {
+        const double w = ws_weight(i0, I, ncx, inv, 2);
+        if (w == 0.0) continue;
+        const int i = i0 + 1;
+        const double diag = 6.0 - (i == 1) - (k == 1) - (k == g.nz) + (i == g.nx);
+        const double pv = P(i, j, k);
+        const double nb = (P(i - 1, j, k) + P(i + 1, j, k)) + (P(i, jm, k) + P(i, jp, k)) +
+                          (P(i, j, k - 1) + P(i, j, k + 1));
+        sr += w * ((double)b[ws_at(g, i, j, k)] - (nb - diag * pv) * r2);
+        sp += w * pv;
     }
-    if (lane == 0 && q < nc) {
-        rc[q] = sr[threadIdx.x] / f3;
-        pc[q] = sp[threadIdx.x] / f3;
+    ar[q] = sr;
+    ap[q] = sp;
+}
+
+// Pass y (periodic): (nz, ny, ncx) -> (nz, ncy, ncx).
+__global__ void __launch_bounds__(WS_THREADS)
+ws_fw_y_kernel(const double *__restrict__ ar, const double *__restrict__ ap, int nz, int ny, int ncx, int f,
+               double *__restrict__ br, double *__restrict__ bp)
+{
+    const int ncy = ny / f;
+    const long long n = (long long)nz * ncy * ncx;
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const int I = (int)(q % ncx), J = (int)((q / ncx) % ncy), k = (int)(q / ((long long)ncx * ncy));
+    const double inv = 1.0 / f;
+    double sr = 0.0, sp = 0.0;
+    for (int j0 = J * f - f / 2; j0 < J * f + (3 * f) / 2; ++j0) {
+        const int jw = ((j0 % ny) + ny) % ny;
+        const double w = ws_weight(jw, J, ncy, inv, 1);
+        if (w == 0.0) continue;
+        const long long src = ((long long)k * ny + jw) * ncx + I;
+        sr += w * ar[src];
+        sp += w * ap[src];
     }
+    br[q] = sr;
+    bp[q] = sp;
+}
+
+// Pass z (Neumann) and the 1/f^3 normalisation: (nz, ncy, ncx) -> rc, pc.
+__global__ void __launch_bounds__(WS_THREADS)
+ws_fw_z_kernel(const double *__restrict__ br, const double *__restrict__ bp, int nz, int ncy, int ncx, int f,
+               double *__restrict__ rc, double *__restrict__ pc)
+{
+    const int ncz = nz / f;
+    const long long n = (long long)ncz * ncy * ncx;
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const int I = (int)(q % ncx), J = (int)((q / ncx) % ncy), K = (int)(q / ((long long)ncx * ncy));
+    const double inv = 1.0 / f;
+    double sr = 0.0, sp = 0.0;
+    const int lo = max(K * f - f / 2, 0), hi = min(K * f + (3 * f) / 2, nz);
+    for (int k0 = lo; k0 < hi; ++k0) {
+        const double w = ws_weight(k0, K, ncz, inv, 0);
+        if (w == 0.0) continue;
+        const long long src = ((long long)k0 * ncy + J) * ncx + I;
+        sr += w * br[src];
+        sp += w * bp[src];
+    }
+    const double norm = inv * inv * inv;
+    rc[q] = sr * norm;
+    pc[q] = sp * norm;
 }
 
 // Single CTA: the two RMS values, the scaled input and s.
@@ -149,14 +211,24 @@ bool ws_factor_ok(int nx, int ny, int nz, int f)
     return nx % f == 0 && ny % f == 0 && nz % f == 0;
 }
 
-gbsw_status launch_ws_restrict(const float *b, const double *p, const WsGrid &g, double dx, int f, double *rc,
-                               double *pc, cudaStream_t s)
+size_t ws_scratch_doubles(int nx, int ny, int nz, int f)
+{
+    const size_t ncx = (size_t)(nx / f), ncy = (size_t)(ny / f);
+    return 2 * (size_t)nz * ny * ncx + 2 * (size_t)nz * ncy * ncx;
+}
+
+gbsw_status launch_ws_restrict(const float *b, const double *p, const WsGrid &g, double dx, int f, double *scratch,
+                               double *rc, double *pc, cudaStream_t s)
 {
     if (!ws_factor_ok(g.nx, g.ny, g.nz, f)) return GBSW_ERR_ARG;
-    const long long nc = (long long)(g.nx / f) * (g.ny / f) * (g.nz / f);
-    const int f3 = f * f * f;
-    const int per_cta = WS_THREADS / (f3 < WS_THREADS ? f3 : WS_THREADS);
-    ws_restrict_kernel<<<(unsigned)((nc + per_cta - 1) / per_cta), WS_THREADS, 0, s>>>(b, p, g, dx, f, rc, pc);
+    const int ncx = g.nx / f, ncy = g.ny / f;
+    const long long n1 = (long long)g.nz * g.ny * ncx, n2 = (long long)g.nz * ncy * ncx;
+    const long long nc = (long long)(g.nz / f) * ncy * ncx;
+    double *ar = scratch, *ap = ar + n1, *br = ap + n1, *bp = br + n2;
+    auto blocks = [](long long n) { return (unsigned)((n + WS_THREADS - 1) / WS_THREADS); };
+    ws_fw_x_kernel<<<blocks(n1), WS_THREADS, 0, s>>>(b, p, g, dx, f, ar, ap);
+    ws_fw_y_kernel<<<blocks(n2), WS_THREADS, 0, s>>>(ar, ap, g.nz, g.ny, ncx, f, br, bp);
+    ws_fw_z_kernel<<<blocks(nc), WS_THREADS, 0, s>>>(br, bp, g.nz, ncy, ncx, f, rc, pc);
     GBSW_LAUNCH_CHECK();
     return GBSW_OK;
 }
@@ -208,13 +280,14 @@ extern "C" gbsw_status warm_start_features(int nx, int ny, int nz, double dx, in
     const long long nc = (long long)(nx / f) * (ny / f) * (nz / f);
     double *buf = nullptr;
     gbsw_status st = GBSW_OK;
-    cudaError_t e = cudaMalloc((void **)&buf, (size_t)(2 * nc + 1) * sizeof(double));
+    cudaError_t e =
+        cudaMalloc((void **)&buf, (size_t)(2 * nc + 1 + ws_scratch_doubles(nx, ny, nz, f)) * sizeof(double));
     if (e != cudaSuccess) {
         record_cuda_error(e, "cudaMalloc", __FILE__, __LINE__);
         return GBSW_ERR_OOM;
     }
     const WsGrid g = dense_grid(nx, ny, nz);
-    st = launch_ws_restrict(b, p, g, dx, f, buf, buf + nc, s);
+    st = launch_ws_restrict(b, p, g, dx, f, buf + 2 * nc + 1, buf, buf + nc, s);
     if (st == GBSW_OK) st = launch_ws_prepare(buf, buf + nc, nc, (f * dx) * (f * dx), x, buf + 2 * nc, s);
     if (st == GBSW_OK) {
         if ((e = cudaMemcpyAsync(scale, buf + 2 * nc, sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||

@@ -16,9 +16,13 @@ struct WsGrid {
 // f a power of two (<= 64) dividing nx, ny and nz.
 bool ws_factor_ok(int nx, int ny, int nz, int f);
 
-// rc, pc: (nz/f)(ny/f)(nx/f) FP64 block means of b - A p and of p.
-gbsw_status launch_ws_restrict(const float *b, const double *p, const WsGrid &g, double dx, int f, double *rc,
-                               double *pc, cudaStream_t s);
+// Doubles of scratch that launch_ws_restrict needs.
+size_t ws_scratch_doubles(int nx, int ny, int nz, int f);
+
+// rc, pc: (nz/f)(ny/f)(nx/f) FP64 full-weighted restrictions of b - A p and
+// of p (prolong^T / f^3).
+gbsw_status launch_ws_restrict(const float *b, const double *p, const WsGrid &g, double dx, int f, double *scratch,
+                               double *rc, double *pc, cudaStream_t s);
 // xin (nc x 2 FP32) and *scale = hc2 * rms(rc) (device).
 gbsw_status launch_ws_prepare(const double *rc, const double *pc, long long nc, double hc2, float *xin,
                               double *scale, cudaStream_t s);

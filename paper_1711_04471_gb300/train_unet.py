@@ -1,14 +1,25 @@
 """Train the warm-start U-Net on pressure increments produced by the plain
 solver, and compare the learned warm start with the plain one.
 
-Training data (the recipe of the learned warm start): LES runs on a
-128 x 128 x 64 grid (dx = 4 m, the same physics and building statistics as
-the 256 x 256 x 128 workload, other building seeds), each step's
-right-hand side b, previous pressure p_prev and converged pressure p
-(relative residual 1e-6), cut into 64^3 crops.  Input channels
-[b dx^2 / s, p_prev / s], target (p - p_prev) / s, s = dx^2 rms(b) over the
-crop.  Everything runs through the C ABI (les_*, unet_*); the samples stay
-in device memory.
+Training data (the recipe of the learned warm start): LES runs on the
+256 x 256 x 128 workload grid (dx = 4 m, 20 % building cover) with other
+building seeds than the evaluation run: the 32 steps after the first 17
+(the stage of the run that is evaluated; the first steps, dominated by the
+start-up transient, are solved to a looser tolerance and not used).  From each step the plain solve's
+previous pressure p_prev, right-hand side b and converged pressure p
+(relative residual 1e-6) give one pair on the grid coarsened by f:
+
+    input   warm_start_features(p_prev, b)            (coarse residual and pressure)
+    target  block mean of (p - p_prev) / s             (s from the same call)
+
+The map from (b, p_prev) to p - p_prev = A^-1 (b - A p_prev) is linear and
+commutes with translations and reflections in y (periodic) and with a sign
+change, so each solved step also yields the pairs of its copies shifted by
+multiples of f and mirrored (32 pairs per step at f = 16, formed from the
+coarse tensors by augment), and any linear combination of pairs is a pair
+(mixed_batch draws the training batches that way).
+Everything runs through the C ABI (les_*, warm_start_*, unet_*); the samples
+stay in device memory.
 
     python -m paper_1711_04471_gb300.train_unet --out weights.npy
 """
@@ -21,75 +32,150 @@ import time
 import numpy as np
 
 
-def generate(nseeds=16, steps=50, spinup=10, crops=6, shape=(128, 128, 64), crop=64, dx=4.0, base_seed=2000,
+def _block_mean(a, f):
+    nz, ny, nx = a.shape
+    return a.reshape(nz // f, f, ny // f, f, nx // f, f).mean(axis=(1, 3, 5))
+
+
+def pair_from_step(p_prev, b, p_new, dx, f):
+    """Coarse input (D/f, H/f, W/f, 2), target (D/f, H/f, W/f) and scale s of
+    one solved step (CUDA float32 tensors, float), or None when the residual
+    is 0.  p_prev, p_new: host float64 interiors; b: host float32 interior."""
+    import torch
+
+    from .les import warm_start_features
+    x, s = warm_start_features(torch.from_numpy(np.ascontiguousarray(p_prev)).cuda(),
+                               torch.from_numpy(np.ascontiguousarray(b)).cuda(), dx, f)
+    if not s > 0:
+        return None
+    t = torch.from_numpy((_block_mean(p_new - p_prev, f) / s).astype(np.float32)).cuda()
+    return x, t, s
+
+
+def augment(X, T, S, mirror=True):
+    """Copies shifted by every multiple of f in y and mirrored in y.  Such
+    shifts and mirrors move whole f-blocks, so the copies' inputs and targets
+    are the coarse tensors rolled and flipped."""
+    import torch
+    xs, ts = [], []
+    for flip in ([False, True] if mirror else [False]):
+        xf, tf = (X.flip(2), T.flip(2)) if flip else (X, T)
+        for o in range(T.shape[2]):
+            xs.append(torch.roll(xf, o, 2))
+            ts.append(torch.roll(tf, o, 2))
+    k = len(xs)
+    return torch.cat(xs).contiguous(), torch.cat(ts).contiguous(), S.repeat(k)
+
+
+def mixed_batch(X, T, S, idx_a, idx_b, gen):
+    """Training batch of random linear combinations of solved pairs.
+
+    With u = s x[..., 0] (the coarse residual times (f dx)^2) and v = s t
+    (the coarse increment), alpha u_a + beta u_b and alpha v_a + beta v_b are
+    again a residual and its increment (the map is linear); the pair is
+    renormalised by s' = rms(u).  The pressure channel is taken from a
+    third, unrelated sample: the increment is fixed by the residual alone,
+    so the network must not learn to read it from the previous pressure."""
+    import torch
+    n = idx_a.numel()
+    ab = torch.randn((2, n), generator=gen, device="cpu")
+    ab[1] *= (torch.rand(n, generator=gen) < 0.5).float()   # half the batch: one pair, random sign and scale
+    ab = ab.to(X.device)
+    sa, sb = S[idx_a].view(n, 1, 1, 1), S[idx_b].view(n, 1, 1, 1)
+    u = ab[0].view(n, 1, 1, 1) * sa * X[idx_a, ..., 0] + ab[1].view(n, 1, 1, 1) * sb * X[idx_b, ..., 0]
+    v = ab[0].view(n, 1, 1, 1) * sa * T[idx_a] + ab[1].view(n, 1, 1, 1) * sb * T[idx_b]
+    r = u.pow(2).mean(dim=(1, 2, 3), keepdim=True).sqrt().clamp_min(1e-30)
+    idx_c = torch.randint(0, X.shape[0], (n,), generator=gen, device="cpu").to(X.device)
+    x = torch.stack([u / r, X[idx_c, ..., 1]], dim=-1)
+    return x.contiguous(), (v / r).contiguous()
+
+
+def generate(nseeds=8, steps=32, start=17, shape=(256, 256, 128), dx=4.0, f=16, base_seed=2000, spinup_tol=1e-4,
              log=print):
-    """Return (X, T) CUDA tensors of shape (n, crop, crop, crop, 2) and (n, crop, crop, crop)."""
+    """Per-seed (X, T, S) CUDA tensors of the solved steps, X (n, D/f, H/f,
+    W/f, 2), T (n, D/f, H/f, W/f), S (n,) FP32 scales.  The first start - 1
+    steps solve to spinup_tol (they only bring the flow to the stage that
+    is evaluated), the next one to 1e-6 so that p_prev of the first pair is
+    a converged pressure."""
     import torch
 
     from . import inputs
     from .les import LES
     nx, ny, nz = shape
-    X, T = [], []
+    out = []
     t0 = time.time()
+    iters = []
     for sd in range(nseeds):
         solid = inputs.les_buildings(nx, ny, nz, dx=dx, seed=inputs.derive_seed(base_seed, sd))
-        rng = inputs.SplitMix64(inputs.derive_seed(base_seed + 1, sd))
-        with LES(nx, ny, nz, solid, check_every=50, max_iter=200000) as les:
-            les.step(spinup, stats=False)
-            for _ in range(steps):
-                p_prev = les.get("p")[1:-1, 1:-1, 1:-1]
+        X, T, S = [], [], []
+        with LES(nx, ny, nz, solid, dx=dx, check_every=50, max_iter=200000) as les:
+            if start > 1:
+                les.set_solver(tol=spinup_tol)
+                les.step(start - 1, stats=False)
+                les.set_solver(tol=1e-6)
+            if start > 0:
                 les.step(1, stats=False)
-                b = les.get("b")[1:-1, 1:-1, 1:-1].astype(np.float64)
-                p = les.get("p")[1:-1, 1:-1, 1:-1]
-                off = rng.uniform(3 * crops)
-                for c in range(crops):
-                    z0 = int(off[3 * c] * (nz - crop + 1))
-                    y0 = int(off[3 * c + 1] * (ny - crop + 1))
-                    x0 = int(off[3 * c + 2] * (nx - crop + 1))
-                    sl = (slice(z0, z0 + crop), slice(y0, y0 + crop), slice(x0, x0 + crop))
-                    bb, pp, pn = b[sl], p_prev[sl], p[sl]
-                    s = dx * dx * math.sqrt(float(np.mean(bb * bb)))
-                    if not s > 0:
-                        continue
-                    x = np.stack([bb * dx * dx / s, pp / s], axis=-1).astype(np.float32)
-                    t = ((pn - pp) / s).astype(np.float32)
-                    X.append(torch.from_numpy(x).cuda())
-                    T.append(torch.from_numpy(t).cuda())
-        log(f"seed {sd}: {len(X)} samples, {time.time() - t0:.0f} s")
-    return torch.stack(X), torch.stack(T)
+            p_prev = les.get("p")[1:-1, 1:-1, 1:-1].copy()
+            for _ in range(steps):
+                st = les.step(1)[0]
+                iters.append(st["iters"])
+                b = les.get("b")[1:-1, 1:-1, 1:-1].copy()
+                p_new = les.get("p")[1:-1, 1:-1, 1:-1].copy()
+                pr = pair_from_step(p_prev, b, p_new, dx, f)
+                if pr is not None:
+                    X.append(pr[0])
+                    T.append(pr[1])
+                    S.append(pr[2])
+                p_prev = p_new
+        out.append((torch.stack(X), torch.stack(T), torch.tensor(S, dtype=torch.float32, device="cuda")))
+        log(f"seed {sd}: {len(X)} steps, mean SOR iterations {np.mean(iters):.0f}, {time.time() - t0:.0f} s")
+    return out
 
 
-def train(net, X, T, iters=3000, batch=4, lr=1e-3, val_frac=0.05, seed=0, log=print):
-    """Adam with cosine decay on random minibatches; returns a summary dict."""
+def slow_mode_error(y, t):
+    """Median relative error of the amplitude of the slowest SOR mode
+    (quarter cosine along x, constant in y and z) of prediction y vs target t,
+    both (n, D, H, W) CUDA tensors."""
     import torch
-    n = X.shape[0]
-    nval = max(1, int(n * val_frac))
-    rng = np.random.default_rng(seed)
-    perm = rng.permutation(n)
-    val, tr = perm[:nval], perm[nval:]
+    W = t.shape[-1]
+    x = torch.arange(W, device=t.device, dtype=torch.float64) + 0.5
+    phi = torch.cos(math.pi * x / (2 * W))
+    a_t = (t.double().mean(dim=(1, 2)) * phi).sum(-1)
+    a_y = (y.double().mean(dim=(1, 2)) * phi).sum(-1)
+    return float(((a_y - a_t).abs() / a_t.abs().clamp_min(1e-30)).median())
 
-    def val_loss():
-        tot, base = 0.0, 0.0
-        for k in range(0, nval, batch):
-            idx = torch.as_tensor(val[k:k + batch], device=X.device)
-            xb, tb = X[idx].contiguous(), T[idx].contiguous()
-            y = net.forward(xb)
-            tot += float(((y - tb) ** 2).sum())
-            base += float((tb ** 2).sum())
-        return tot / base   # relative to the zero-increment predictor (the plain warm start)
+
+def train(net, Xtr, Ttr, Str, Xval, Tval, iters=10000, batch=32, lr=1e-3, seed=0, log=print):
+    """Adam with cosine decay on mixed minibatches (mixed_batch); returns a
+    summary dict.  val_rel is the error energy relative to the zero
+    increment (the plain warm start's coarse error) on held-out pairs."""
+    import torch
+    n = Xtr.shape[0]
+    gen = torch.Generator().manual_seed(seed)
+
+    def evaluate():
+        ys = []
+        for k in range(0, Xval.shape[0], batch):
+            ys.append(net.forward(Xval[k:k + batch].contiguous()))
+        y = torch.cat(ys)
+        rel = float(((y - Tval) ** 2).sum() / (Tval ** 2).sum())
+        return rel, slow_mode_error(y, Tval)
 
     hist = []
     t0 = time.time()
     for it in range(iters):
-        idx = torch.as_tensor(rng.choice(tr, size=batch, replace=False), device=X.device)
+        ia = torch.randint(0, n, (batch,), generator=gen).to(Xtr.device)
+        ib = torch.randint(0, n, (batch,), generator=gen).to(Xtr.device)
+        x, t = mixed_batch(Xtr, Ttr, Str, ia, ib, gen)
         lr_t = lr * 0.5 * (1.0 + math.cos(math.pi * it / iters))
-        loss = net.train_step(X[idx].contiguous(), T[idx].contiguous(), lr_t)
-        hist.append(loss)
+        hist.append(net.train_step(x, t, lr_t))
         if (it + 1) % max(1, iters // 10) == 0:
-            log(f"iter {it + 1}: train loss {np.mean(hist[-50:]):.4e}, val rel {val_loss():.4f}, "
-                f"{time.time() - t0:.0f} s")
-    return dict(train_loss=float(np.mean(hist[-50:])), val_rel=val_loss(), seconds=time.time() - t0,
-                samples=int(n), iters=iters, batch=batch)
+            rel, slow = evaluate()
+            log(f"iter {it + 1}: train loss {np.mean(hist[-100:]):.4e}, val rel {rel:.4f}, "
+                f"slow-mode err {slow:.4f}, {time.time() - t0:.0f} s")
+    rel, slow = evaluate()
+    return dict(train_loss=float(np.mean(hist[-100:])), val_rel=rel, val_slow_mode_err=slow,
+                seconds=time.time() - t0, samples=int(n), val_samples=int(Xval.shape[0]), iters=iters, batch=batch)
 
 
 def compare_warm_starts(net, shape=(256, 256, 128), seed=1003, spinup=20, steps=10, log=print, **les_kw):
@@ -118,30 +204,54 @@ def compare_warm_starts(net, shape=(256, 256, 128), seed=1003, spinup=20, steps=
                              nn_ms=b["ms_predictor"] + b["ms_guess"] + b["ms_solve"], nn_guess_ms=b["ms_guess"],
                              plain_res=a["rel_res"], nn_res=b["rel_res"]))
             log(f"step {count}: plain {a['iters']} it {rows[-1]['plain_ms']:.0f} ms | "
-                f"nn {b['iters']} it {rows[-1]['nn_ms']:.0f} ms (guess {b['ms_guess']:.1f} ms)")
+                f"nn {b['iters']} it {rows[-1]['nn_ms']:.0f} ms (guess {b['ms_guess']:.2f} ms)")
     return rows
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", required=True)
-    ap.add_argument("--seeds", type=int, default=16)
-    ap.add_argument("--steps", type=int, default=50)
-    ap.add_argument("--crops", type=int, default=6)
-    ap.add_argument("--iters", type=int, default=3000)
-    ap.add_argument("--batch", type=int, default=4)
+    ap.add_argument("--seeds", type=int, default=8, help="LES runs (building seeds); the last one is held out")
+    ap.add_argument("--steps", type=int, default=32, help="solved steps per run")
+    ap.add_argument("--start", type=int, default=17, help="steps before the first pair")
+    ap.add_argument("--factor", type=int, default=16)
+    ap.add_argument("--data", help="load the solved pairs from this .npz instead of running the LES")
+    ap.add_argument("--save-data", help="write the solved pairs to this .npz")
+    ap.add_argument("--iters", type=int, default=20000)
+    ap.add_argument("--batch", type=int, default=32)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--init-seed", type=int, default=0)
+    ap.add_argument("--compare-steps", type=int, default=0, help="paired evaluation steps after training")
     args = ap.parse_args()
+    import torch
+
     from . import build
     build()
     from .unet import UNet
-    X, T = generate(args.seeds, args.steps, crops=args.crops)
-    print(f"data: {tuple(X.shape)} inputs, target rms {float(T.pow(2).mean().sqrt()):.3e}", flush=True)
+    if args.data:
+        z = np.load(args.data)
+        data = [tuple(torch.from_numpy(z[f"{a}{k}"]).cuda() for a in "xts") for k in range(int(z["nseeds"]))]
+    else:
+        data = generate(args.seeds, args.steps, start=args.start, f=args.factor)
+    if args.save_data:
+        arrs = {"nseeds": np.array(len(data))}
+        for k, (x, t, s) in enumerate(data):
+            arrs[f"x{k}"], arrs[f"t{k}"], arrs[f"s{k}"] = x.cpu().numpy(), t.cpu().numpy(), s.cpu().numpy()
+        np.savez_compressed(args.save_data, **arrs)
+    Xtr, Ttr, Str = augment(torch.cat([d[0] for d in data[:-1]]), torch.cat([d[1] for d in data[:-1]]),
+                            torch.cat([d[2] for d in data[:-1]]))
+    Xval, Tval, _ = data[-1]
+    print(f"data: {tuple(Xtr.shape)} train (shifted and mirrored), {tuple(Xval.shape)} held out, "
+          f"target rms {float(Ttr.pow(2).mean().sqrt()):.3e}", flush=True)
     with UNet(seed=args.init_seed) as net:
-        summary = train(net, X, T, iters=args.iters, batch=args.batch, lr=args.lr)
+        summary = train(net, Xtr, Ttr, Str, Xval, Tval, iters=args.iters, batch=args.batch, lr=args.lr)
         print(summary, flush=True)
         np.save(args.out, net.get_params())
+        if args.compare_steps:
+            rows = compare_warm_starts(net, steps=args.compare_steps)
+            pi = np.mean([r["plain_iters"] for r in rows])
+            ni = np.mean([r["nn_iters"] for r in rows])
+            print(f"paired: plain {pi:.0f} it, learned {ni:.0f} it", flush=True)
 
 
 if __name__ == "__main__":
