@@ -1,8 +1,14 @@
 // Red-black SOR pressure solve ("press", Sec. 6.3.1 of arXiv:1711.04471)
 // with an FP64 residual norm and a device-side convergence test: one solve
 // is one launch of a CUDA graph whose while-node repeats
-// [m SOR iterations, FP64 residual, test] until ||b - A p|| <= tol ||b||
+// [m SOR iterations, fold, FP64 residual, test] until ||b - A p|| <= tol ||b||
 // or max_iter, with no host round trip.
+//
+// FP64 runs at a small fraction of the FP32 rate on this GPU, so the check
+// is arranged to spend few FP64 operations per cell: the FP32 correction is
+// folded into the FP64 base once per check (2 operations per cell), the
+// residual is then a plain FP64 stencil of the base (no per-neighbour
+// conversion), and ||b||^2 is formed once per solve.
 #include <math.h>
 #include <stdlib.h>
 
@@ -33,7 +39,8 @@ __device__ __forceinline__ float pdiag(const PDims &d, int i, int k)
 // (j, 2kp+1) and (j, 2kp+2): two independent updates per thread keep more
 // loads in flight.
 // FIRST: first iteration after a residual check; the correction restarts
-// from 0 (the old correction is folded into p_hi first).
+// from 0 (the fold before the check has zeroed it), so the first red
+// half-sweep reads no neighbours and no old value.
 // Launch: grid (ceil(((nx+1)/2) / 128), ny, ceil(nz/2)), block 128.
 template <bool FIRST>
 __global__ void __launch_bounds__(128)
@@ -60,12 +67,7 @@ sor_sweep_kernel(PDims d, int colour, float omega, float h2, float *__restrict__
         cc[h] = c;
         upd[h] = 0.0f;
         if (!ok[h]) continue;
-        float e_old = 0.0f;
-        if (FIRST) {
-            p_hi[pidx(d, i, j, k)] += (double)ec[c];
-        } else {
-            e_old = ec[c];
-        }
+        const float e_old = FIRST ? 0.0f : ec[c];
         float s = 0.0f;
         if (need_nb) {
             const long long row = (long long)k * d.cplane;
@@ -80,52 +82,63 @@ sor_sweep_kernel(PDims d, int colour, float omega, float h2, float *__restrict__
         if (ok[h]) ec[cc[h]] = upd[h];
 }
 
-// r = b - A (p_hi + e) in FP64 (stored as FP32 in the colour arrays), with
-// block partial sums of ||r||^2 and ||b||^2.  Grid-stride over the interior
-// with a fixed grid.
+// r = b - A p_hi in FP64 (the correction has been folded into p_hi; r is
+// stored as FP32 in the colour arrays), with block partial sums of ||r||^2
+// and, with WITH_BB (once per solve), of ||b||^2.  Block (bx, j, bz): 256
+// cells of row j from i = 256 bx + 1, planes 8 bz + 1 .. 8 bz + 8 (no index
+// division).  A p_hi = (sum of neighbours - d_c p) / dx^2 with
+// d_c = 6 - [i == 1] - [k == 1] - [k == nz] + [i == nx] is formed as
+// sum - 6 p plus the boundary terms, so that interior cells take 6 FP64
+// additions and one FMA.
+template <bool WITH_BB>
 __global__ void __launch_bounds__(POI_RED_THREADS)
-poisson_resid_kernel(PDims d, const float *__restrict__ b, const double *__restrict__ p_hi,
-                     const float *__restrict__ e0, const float *__restrict__ e1, float *__restrict__ r0,
+poisson_resid_kernel(PDims d, const float *__restrict__ b, const double *__restrict__ p_hi, float *__restrict__ r0,
                      float *__restrict__ r1, double *__restrict__ partials)
 {
     __shared__ double red[POI_RED_THREADS / 32];
     const double r2 = 1.0 / (d.dx * d.dx);
-    const long long total = (long long)d.nx * d.ny * d.nz;
+    const int i = blockIdx.x * POI_RED_THREADS + threadIdx.x + 1;
+    const int j = blockIdx.y + 1;
+    const int jm = (j == 1) ? d.ny : j - 1;
+    const int jp = (j == d.ny) ? 1 : j + 1;
     double rr = 0.0, bb = 0.0;
-    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total;
-         q += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(q % d.nx) + 1;
-        const long long t = q / d.nx;
-        const int j = (int)(t % d.ny) + 1;
-        const int k = (int)(t / d.ny) + 1;
-        const int jm = (j == 1) ? d.ny : j - 1;
-        const int jp = (j == d.ny) ? 1 : j + 1;
-        // p at a cell: FP64 base + FP32 correction of that cell's colour;
+    if (i <= d.nx) {
         // cells outside the grid in x or z read as 0 (ghost values unused)
         auto P = [&](int ii, int jj, int kk) -> double {
             if (ii < 1 || ii > d.nx || kk < 1 || kk > d.nz) return 0.0;
-            const float *ea = ((ii + jj + kk) & 1) ? e1 : e0;
-            return p_hi[pidx(d, ii, jj, kk)] + (double)ea[cidx(d, ii, jj, kk)];
+            return p_hi[pidx(d, ii, jj, kk)];
         };
-        const double s = (P(i - 1, j, k) + P(i + 1, j, k)) + (P(i, jm, k) + P(i, jp, k)) +
-                         (P(i, j, k - 1) + P(i, j, k + 1));
-        const double bc = (double)b[pidx(d, i, j, k)];
-        const double res = bc - (s - (double)pdiag(d, i, k) * P(i, j, k)) * r2;
-        float *ra = ((i + j + k) & 1) ? r1 : r0;
-        ra[cidx(d, i, j, k)] = (float)res;
-        rr += res * res;
-        bb += bc * bc;
+        for (int kk = 0; kk < POI_RES_PLANES; ++kk) {
+            const int k = blockIdx.z * POI_RES_PLANES + kk + 1;
+            if (k > d.nz) break;
+            const double pc = p_hi[pidx(d, i, j, k)];
+            const double nb = (P(i - 1, j, k) + P(i + 1, j, k)) + (P(i, jm, k) + P(i, jp, k)) +
+                              (P(i, j, k - 1) + P(i, j, k + 1));
+            double s = fma(-6.0, pc, nb);
+            if (i == 1) s += pc;
+            if (k == 1) s += pc;
+            if (k == d.nz) s += pc;
+            if (i == d.nx) s -= pc;
+            const double bc = (double)b[pidx(d, i, j, k)];
+            const double res = fma(-s, r2, bc);
+            float *ra = ((i + j + k) & 1) ? r1 : r0;
+            ra[cidx(d, i, j, k)] = (float)res;
+            rr = fma(res, res, rr);
+            if (WITH_BB) bb = fma(bc, bc, bb);
+        }
     }
     rr = block_sum_f64<POI_RED_THREADS / 32>(rr, red);
-    bb = block_sum_f64<POI_RED_THREADS / 32>(bb, red);
+    if (WITH_BB) bb = block_sum_f64<POI_RED_THREADS / 32>(bb, red);
     if (threadIdx.x == 0) {
-        partials[2 * blockIdx.x] = rr;
-        partials[2 * blockIdx.x + 1] = bb;
+        const int blk = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+        partials[2 * blk] = rr;
+        if (WITH_BB) partials[2 * blk + 1] = bb;
     }
 }
 
 // Folds the partials (fixed order), updates the control block and sets the
 // while-node condition: continue while rho > tol and iters < max_iter.
+// The ||b||^2 partials are those of the solve's first residual.
 template <bool GRAPH>
 __global__ void __launch_bounds__(POI_RED_THREADS)
 poisson_test_kernel(const double *__restrict__ partials, int nblocks, PoissonCtl *ctl, double tol, int max_iter,
@@ -158,7 +171,7 @@ poisson_test_kernel(const double *__restrict__ partials, int nblocks, PoissonCtl
     }
 }
 
-// p_hi += e, e = 0 on the interior cells of one colour (end of a solve).
+// p_hi += e, e = 0 on the interior cells of one colour (before each check).
 __global__ void poisson_fold_kernel(PDims d, int colour, double *__restrict__ p_hi, float *__restrict__ ec)
 {
     const int slot = blockIdx.x * blockDim.x + threadIdx.x;
@@ -215,7 +228,9 @@ gbsw_status PoissonSolver::init(int nx, int ny, int nz, double dx, const float *
         GBSW_CUDA_TRY(cudaMemsetAsync(e[c], 0, nc * sizeof(float), stream));
         GBSW_CUDA_TRY(cudaMemsetAsync(r[c], 0, nc * sizeof(float), stream));
     }
-    GBSW_CUDA_TRY(cudaMalloc((void **)&partials, 2 * POI_RED_BLOCKS * sizeof(double)));
+    rgrid = dim3(ceil_div(nx, POI_RED_THREADS), ny, ceil_div(nz, POI_RES_PLANES));
+    rblocks = (int)(rgrid.x * rgrid.y * rgrid.z);
+    GBSW_CUDA_TRY(cudaMalloc((void **)&partials, 2 * (size_t)rblocks * sizeof(double)));
     GBSW_CUDA_TRY(cudaMalloc((void **)&ctl, sizeof(PoissonCtl)));
     GBSW_CUDA_TRY(cudaMemsetAsync(ctl, 0, sizeof(PoissonCtl), stream));
     dirty_ = true;
@@ -280,13 +295,12 @@ gbsw_status PoissonSolver::build_graph()
     chk(cudaGraphConditionalHandleCreate(&handle, graph_, 0, cudaGraphCondAssignDefault));
     chk(cudaStreamBeginCaptureToGraph(cs, graph_, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     if (err == cudaSuccess) {
-        // prelude: e = 0, r = b - A p_hi, first test
+        // prelude: e = 0, r = b - A p_hi, ||b||^2, first test
         chk(cudaMemsetAsync(e[0], 0, nc * sizeof(float), cs));
         chk(cudaMemsetAsync(e[1], 0, nc * sizeof(float), cs));
-        poisson_resid_kernel<<<POI_RED_BLOCKS, POI_RED_THREADS, 0, cs>>>(d, b, p_hi, e[0], e[1], r[0], r[1],
-                                                                        partials);
+        poisson_resid_kernel<true><<<rgrid, POI_RED_THREADS, 0, cs>>>(d, b, p_hi, r[0], r[1], partials);
         chk(cudaGetLastError());
-        poisson_test_kernel<true><<<1, POI_RED_THREADS, 0, cs>>>(partials, POI_RED_BLOCKS, ctl, tol, max_iter, m, 0,
+        poisson_test_kernel<true><<<1, POI_RED_THREADS, 0, cs>>>(partials, rblocks, ctl, tol, max_iter, m, 0,
                                                                   handle);
         chk(cudaGetLastError());
         // while node
@@ -301,16 +315,13 @@ gbsw_status PoissonSolver::build_graph()
         cp.conditional.size = 1;
         if (err == cudaSuccess) chk(cudaGraphAddNode(&cnode, cap_graph, deps, nullptr, ndeps, &cp));
         if (err == cudaSuccess) chk(cudaStreamUpdateCaptureDependencies(cs, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies));
-        // epilogue: fold the last correction
-        poisson_fold_kernel<<<fgrid, sblock, 0, cs>>>(d, 0, p_hi, e[0]);
-        poisson_fold_kernel<<<fgrid, sblock, 0, cs>>>(d, 1, p_hi, e[1]);
-        chk(cudaGetLastError());
     }
     cudaGraph_t captured = nullptr;
     cudaError_t e_end = cudaStreamEndCapture(cs, &captured);
     chk(e_end);
     if (err == cudaSuccess) {
-        // body of the while node: m iterations, residual, test
+        // body of the while node: m iterations, fold, residual, test (the
+        // fold leaves p_hi complete whenever the loop stops)
         body = cp.conditional.phGraph_out[0];
         chk(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
         if (err == cudaSuccess) {
@@ -320,9 +331,10 @@ gbsw_status PoissonSolver::build_graph()
                 sor_sweep_kernel<false><<<sgrid, sblock, 0, cs>>>(d, 0, om, h2, e[0], e[1], r[0], p_hi);
                 sor_sweep_kernel<false><<<sgrid, sblock, 0, cs>>>(d, 1, om, h2, e[1], e[0], r[1], p_hi);
             }
-            poisson_resid_kernel<<<POI_RED_BLOCKS, POI_RED_THREADS, 0, cs>>>(d, b, p_hi, e[0], e[1], r[0], r[1],
-                                                                            partials);
-            poisson_test_kernel<true><<<1, POI_RED_THREADS, 0, cs>>>(partials, POI_RED_BLOCKS, ctl, tol, max_iter, m,
+            poisson_fold_kernel<<<fgrid, sblock, 0, cs>>>(d, 0, p_hi, e[0]);
+            poisson_fold_kernel<<<fgrid, sblock, 0, cs>>>(d, 1, p_hi, e[1]);
+            poisson_resid_kernel<false><<<rgrid, POI_RED_THREADS, 0, cs>>>(d, b, p_hi, r[0], r[1], partials);
+            poisson_test_kernel<true><<<1, POI_RED_THREADS, 0, cs>>>(partials, rblocks, ctl, tol, max_iter, m,
                                                                     1, handle);
             chk(cudaGetLastError());
         }
@@ -358,9 +370,8 @@ gbsw_status PoissonSolver::enqueue_fixed(int niter)
     const dim3 fgrid(ceil_div((d.nx + 1) / 2, 128), d.ny, d.nz);
     GBSW_CUDA_TRY(cudaMemsetAsync(e[0], 0, nc * sizeof(float), stream));
     GBSW_CUDA_TRY(cudaMemsetAsync(e[1], 0, nc * sizeof(float), stream));
-    poisson_resid_kernel<<<POI_RED_BLOCKS, POI_RED_THREADS, 0, stream>>>(d, b, p_hi, e[0], e[1], r[0], r[1],
-                                                                        partials);
-    poisson_test_kernel<false><<<1, POI_RED_THREADS, 0, stream>>>(partials, POI_RED_BLOCKS, ctl, 0.0, niter, 0, 0, 0);
+    poisson_resid_kernel<true><<<rgrid, POI_RED_THREADS, 0, stream>>>(d, b, p_hi, r[0], r[1], partials);
+    poisson_test_kernel<false><<<1, POI_RED_THREADS, 0, stream>>>(partials, rblocks, ctl, 0.0, niter, 0, 0, 0);
     for (int it = 0; it < niter; ++it) {
         if (it == 0) {
             sor_sweep_kernel<true><<<sgrid, sblock, 0, stream>>>(d, 0, om, h2, e[0], e[1], r[0], p_hi);
@@ -370,12 +381,11 @@ gbsw_status PoissonSolver::enqueue_fixed(int niter)
             sor_sweep_kernel<false><<<sgrid, sblock, 0, stream>>>(d, 1, om, h2, e[1], e[0], r[1], p_hi);
         }
     }
-    poisson_resid_kernel<<<POI_RED_BLOCKS, POI_RED_THREADS, 0, stream>>>(d, b, p_hi, e[0], e[1], r[0], r[1],
-                                                                        partials);
-    poisson_test_kernel<false><<<1, POI_RED_THREADS, 0, stream>>>(partials, POI_RED_BLOCKS, ctl, 0.0, niter, niter,
-                                                                   1, 0);
     poisson_fold_kernel<<<fgrid, sblock, 0, stream>>>(d, 0, p_hi, e[0]);
     poisson_fold_kernel<<<fgrid, sblock, 0, stream>>>(d, 1, p_hi, e[1]);
+    poisson_resid_kernel<false><<<rgrid, POI_RED_THREADS, 0, stream>>>(d, b, p_hi, r[0], r[1], partials);
+    poisson_test_kernel<false><<<1, POI_RED_THREADS, 0, stream>>>(partials, rblocks, ctl, 0.0, niter, niter,
+                                                                   1, 0);
     GBSW_LAUNCH_CHECK();
     return GBSW_OK;
 }

@@ -70,7 +70,9 @@ public:
     float *e[2] = {};         // FP32 correction of the inner sweeps, per colour
     float *r[2] = {};         // FP32 residual (right-hand side of the sweeps), per colour
     const float *b = nullptr;
-    double *partials = nullptr;
+    double *partials = nullptr;   // 2 per residual block (||r||^2, ||b||^2)
+    dim3 rgrid;                   // residual grid: (ceil(nx/256), ny, ceil(nz/8)), fixed per size
+    int rblocks = 0;
     PoissonCtl *ctl = nullptr;
     cudaStream_t stream = nullptr;
     double omega = 1.8, tol = 1e-6;
@@ -83,7 +85,7 @@ private:
     bool dirty_ = true;
 };
 
-constexpr int POI_RED_BLOCKS = 2048;   // fixed, so the FP64 sum order is fixed
+constexpr int POI_RES_PLANES = 8;     // z-planes per thread of the residual kernel
 constexpr int POI_RED_THREADS = 256;
 
 }  // namespace gbsw
