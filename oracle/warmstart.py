@@ -84,7 +84,8 @@ def prolong(c: np.ndarray, f: int) -> np.ndarray:
     """Trilinear interpolation of a coarse (ncz, ncy, ncx) field to the fine grid."""
     ncz, ncy, ncx = c.shape
     Wz, Wy, Wx = _weights(ncz * f, ncy * f, ncx * f, f)
-    return np.einsum("zk,yj,xi,kji->zyx", Wz, Wy, Wx, c)
+    # one axis at a time (a sequence of matrix products), not one 6-index loop
+    return np.einsum("zk,yj,xi,kji->zyx", Wz, Wy, Wx, c, optimize=True)
 
 
 def restrict_fw(a: np.ndarray, f: int) -> np.ndarray:
@@ -93,7 +94,7 @@ def restrict_fw(a: np.ndarray, f: int) -> np.ndarray:
     if nz % f or ny % f or nx % f:
         raise ValueError("grid not divisible by f")
     Wz, Wy, Wx = _weights(nz, ny, nx, f)
-    return np.einsum("zk,yj,xi,zyx->kji", Wz, Wy, Wx, a) / f ** 3
+    return np.einsum("zk,yj,xi,zyx->kji", Wz, Wy, Wx, a, optimize=True) / f ** 3
 
 
 def residual_field(P, b: np.ndarray, p: np.ndarray) -> np.ndarray:
