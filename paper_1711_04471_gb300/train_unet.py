@@ -178,10 +178,14 @@ def train(net, Xtr, Ttr, Str, Xval, Tval, iters=10000, batch=32, lr=1e-3, seed=0
                 seconds=time.time() - t0, samples=int(n), val_samples=int(Xval.shape[0]), iters=iters, batch=batch)
 
 
-def compare_warm_starts(net, shape=(256, 256, 128), seed=1003, spinup=20, steps=10, log=print, **les_kw):
+def compare_warm_starts(net, shape=(256, 256, 128), seed=1003, spinup=20, steps=10, log=print, spinup_tol=None,
+                        **les_kw):
     """Paired comparison on the same states: from each state of a plain run,
     one step with the previous-pressure warm start and one with the network,
-    both to the same tolerance.  Returns per-step iterations and times."""
+    both to the same tolerance.  Returns per-step iterations and times.
+    spinup_tol: tolerance of all spin-up steps but the last (None: the
+    solver's own); the last one always solves to the solver's tolerance, so
+    that the first compared step starts from a converged pressure."""
     from . import inputs
     from .les import LES
     nx, ny, nz = shape
@@ -189,7 +193,14 @@ def compare_warm_starts(net, shape=(256, 256, 128), seed=1003, spinup=20, steps=
     names = ("u", "v", "w", "p", "fuo", "fvo", "fwo", "gu", "gv", "gw")
     rows = []
     with LES(nx, ny, nz, solid, **les_kw) as ref, LES(nx, ny, nz, solid, **les_kw) as trial:
-        ref.step(spinup, stats=False)
+        if spinup_tol is not None and spinup > 1:
+            tol = ref.params.tol
+            ref.set_solver(tol=spinup_tol)
+            ref.step(spinup - 1, stats=False)
+            ref.set_solver(tol=tol)
+            ref.step(1, stats=False)
+        else:
+            ref.step(spinup, stats=False)
         trial.set_warm_start(net)
         for k in range(steps):
             state = {n: ref.get(n) for n in names}
