@@ -26,7 +26,7 @@ __device__ __forceinline__ long long pidx(const PDims &d, int i, int j, int k)
 // Slot of cell (i, j, k) in the array of its colour.
 __device__ __forceinline__ long long cidx(const PDims &d, int i, int j, int k)
 {
-    return (long long)k * d.cplane + (long long)j * d.cpitch + 1 + ((i - 1) >> 1);
+    return (long long)k * d.cplane + (long long)j * d.cpitch + SOR_SLOT0 + ((i - 1) >> 1);
 }
 
 __device__ __forceinline__ float pdiag(const PDims &d, int i, int k)
@@ -35,51 +35,70 @@ __device__ __forceinline__ float pdiag(const PDims &d, int i, int k)
 }
 
 // One colour half-sweep over cells with (i + j + k) % 2 == colour.  Thread
-// (slot, j, kp) owns the cells of that colour at slot `slot` of rows
-// (j, 2kp+1) and (j, 2kp+2): two independent updates per thread keep more
-// loads in flight.
+// (g, j, kp) owns the cells of that colour at slots 4g .. 4g+3 of rows
+// (j, SOR_KZ kp + 1 .. SOR_KZ kp + SOR_KZ): every access of a plane is one
+// 16-byte vector (own correction, residual, the other colour's y and z
+// neighbours and its four x neighbours) plus one word (the fifth x
+// neighbour), so a warp covers 128 slots of a row with a few wide loads.
+// The per-cell arithmetic is that of the scalar update
+//   e <- e + omega ((sum of the six neighbours - dx^2 r) / d_c - e)
+// with the neighbour sum associated as (x pair + y pair) + z pair.
+// Slots beyond the last cell of a row are pad words: they are written 0.
 // FIRST: first iteration after a residual check; the correction restarts
 // from 0 (the fold before the check has zeroed it), so the first red
 // half-sweep reads no neighbours and no old value.
-// Launch: grid (ceil(((nx+1)/2) / 128), ny, ceil(nz/2)), block 128.
+// Launch: grid (ceil(((nx+1)/2) / 128), ceil(ny / SOR_ROWS), ceil(nz / SOR_KZ)),
+// block (32, SOR_ROWS).
 template <bool FIRST>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(32 * SOR_ROWS)
 sor_sweep_kernel(PDims d, int colour, float omega, float h2, float *__restrict__ ec, const float *__restrict__ eo,
-                 const float *__restrict__ rc, double *__restrict__ p_hi)
+                 const float *__restrict__ rc)
 {
-    const int slot = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y + 1;
-    const int k0 = 2 * blockIdx.z + 1;
-    if (2 * slot + 1 > d.nx) return;  // no cell of either colour at this slot
+    const int s0 = 4 * (blockIdx.x * 32 + threadIdx.x);
+    const int j = blockIdx.y * SOR_ROWS + threadIdx.y + 1;
+    if (2 * s0 + 1 > d.nx || j > d.ny) return;  // no cell of either colour in this group
     const int jm = (j == 1) ? d.ny : j - 1;
     const int jp = (j == d.ny) ? 1 : j + 1;
     const bool need_nb = !FIRST || colour == 1;  // on the first red half-sweep every neighbour is still 0
-    float upd[2];
-    long long cc[2];
-    bool ok[2];
+    const long long rowj = (long long)j * d.cpitch + SOR_SLOT0 + s0;
+    const long long dym = (long long)(jm - j) * d.cpitch, dyp = (long long)(jp - j) * d.cpitch;
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int k = k0 + h;
+    for (int h = 0; h < SOR_KZ; ++h) {
+        const int k = SOR_KZ * blockIdx.z + 1 + h;
+        if (k > d.nz) break;
         const int q = (colour + 1 + j + k) & 1;
-        const int i = 2 * slot + 1 + q;
-        ok[h] = i <= d.nx && k <= d.nz;
-        const long long c = (long long)k * d.cplane + (long long)j * d.cpitch + 1 + slot;
-        cc[h] = c;
-        upd[h] = 0.0f;
-        if (!ok[h]) continue;
-        const float e_old = FIRST ? 0.0f : ec[c];
-        float s = 0.0f;
+        const long long c = (long long)k * d.cplane + rowj;
+        const float4 e_old = FIRST ? make_float4(0.f, 0.f, 0.f, 0.f) : *reinterpret_cast<const float4 *>(ec + c);
+        const float4 r4 = *reinterpret_cast<const float4 *>(rc + c);
+        float sx[4] = {0.f, 0.f, 0.f, 0.f}, sy[4] = {0.f, 0.f, 0.f, 0.f}, sz[4] = {0.f, 0.f, 0.f, 0.f};
         if (need_nb) {
-            const long long row = (long long)k * d.cplane;
-            s = (eo[c - 1 + q] + eo[c + q]) +
-                (eo[row + (long long)jm * d.cpitch + 1 + slot] + eo[row + (long long)jp * d.cpitch + 1 + slot]) +
-                (eo[c - d.cplane] + eo[c + d.cplane]);
+            const float4 o = *reinterpret_cast<const float4 *>(eo + c);
+            const float4 ym = *reinterpret_cast<const float4 *>(eo + c + dym);
+            const float4 yp = *reinterpret_cast<const float4 *>(eo + c + dyp);
+            const float4 zm = *reinterpret_cast<const float4 *>(eo + c - d.cplane);
+            const float4 zp = *reinterpret_cast<const float4 *>(eo + c + d.cplane);
+            // x neighbours of slot s are slots s - 1 + q and s + q of the other colour
+            if (q == 0) {
+                const float ol = eo[c - 1];
+                sx[0] = ol + o.x; sx[1] = o.x + o.y; sx[2] = o.y + o.z; sx[3] = o.z + o.w;
+            } else {
+                const float orr = eo[c + 4];
+                sx[0] = o.x + o.y; sx[1] = o.y + o.z; sx[2] = o.z + o.w; sx[3] = o.w + orr;
+            }
+            sy[0] = ym.x + yp.x; sy[1] = ym.y + yp.y; sy[2] = ym.z + yp.z; sy[3] = ym.w + yp.w;
+            sz[0] = zm.x + zp.x; sz[1] = zm.y + zp.y; sz[2] = zm.z + zp.z; sz[3] = zm.w + zp.w;
         }
-        upd[h] = e_old + omega * ((s - h2 * rc[c]) / pdiag(d, i, k) - e_old);
-    }
+        const float eo4[4] = {e_old.x, e_old.y, e_old.z, e_old.w};
+        const float rr4[4] = {r4.x, r4.y, r4.z, r4.w};
+        float u[4];
 #pragma unroll
-    for (int h = 0; h < 2; ++h)
-        if (ok[h]) ec[cc[h]] = upd[h];
+        for (int t = 0; t < 4; ++t) {
+            const int i = 2 * (s0 + t) + 1 + q;
+            const float s = need_nb ? (sx[t] + sy[t]) + sz[t] : 0.0f;
+            u[t] = i <= d.nx ? eo4[t] + omega * ((s - h2 * rr4[t]) / pdiag(d, i, k) - eo4[t]) : 0.0f;
+        }
+        *reinterpret_cast<float4 *>(ec + c) = make_float4(u[0], u[1], u[2], u[3]);
+    }
 }
 
 // r = b - A p_hi in FP64 (the correction has been folded into p_hi; r is
@@ -172,13 +191,14 @@ poisson_test_kernel(const double *__restrict__ partials, int nblocks, PoissonCtl
 }
 
 // p_hi += e, e = 0 on the interior cells of one colour (before each check).
+// Launch: grid (ceil(((nx+1)/2) / 128), ny, nz), block 128 (one-dimensional).
 __global__ void poisson_fold_kernel(PDims d, int colour, double *__restrict__ p_hi, float *__restrict__ ec)
 {
     const int slot = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y + 1, k = blockIdx.z + 1;
     const int i = 2 * slot + 1 + ((colour + 1 + j + k) & 1);
     if (i > d.nx) return;
-    const long long c = (long long)k * d.cplane + (long long)j * d.cpitch + 1 + slot;
+    const long long c = (long long)k * d.cplane + (long long)j * d.cpitch + SOR_SLOT0 + slot;
     p_hi[pidx(d, i, j, k)] += (double)ec[c];
     ec[c] = 0.0f;
 }
@@ -206,6 +226,13 @@ __global__ void poisson_gather_kernel(PDims d, const double *__restrict__ src, f
 
 // ---------------------------------------------------------------------------
 
+// Grid of sor_sweep_kernel: 128 slots (32 threads x 4) by SOR_ROWS rows by
+// SOR_KZ planes per block.
+static dim3 sweep_grid(const PDims &d)
+{
+    return dim3(ceil_div((d.nx + 1) / 2, 128), ceil_div(d.ny, SOR_ROWS), ceil_div(d.nz, SOR_KZ));
+}
+
 gbsw_status PoissonSolver::init(int nx, int ny, int nz, double dx, const float *b_dev, cudaStream_t s)
 {
     d.nx = nx;
@@ -213,7 +240,7 @@ gbsw_status PoissonSolver::init(int nx, int ny, int nz, double dx, const float *
     d.nz = nz;
     d.pitch = (int)round_up((size_t)nx + 2, 32);
     d.plane = (long long)(ny + 2) * d.pitch;
-    d.cpitch = (int)round_up((size_t)(nx >> 1) + 2, 4);
+    d.cpitch = SOR_SLOT0 + (int)round_up((size_t)(nx + 1) / 2, 4) + 4;
     d.cplane = (long long)(ny + 2) * d.cpitch;
     d.dx = dx;
     b = b_dev;
@@ -278,8 +305,8 @@ gbsw_status PoissonSolver::build_graph()
     const size_t nc = (size_t)d.cplane * (size_t)(d.nz + 2);
     const float om = (float)omega, h2 = (float)(d.dx * d.dx);
     const int nxh = (d.nx + 1) / 2;
-    const dim3 sgrid(ceil_div(nxh, 128), d.ny, ceil_div(d.nz, 2)), sblock(128);
-    const dim3 fgrid(ceil_div(nxh, 128), d.ny, d.nz);
+    const dim3 sgrid = sweep_grid(d), sblock(32, SOR_ROWS);
+    const dim3 fgrid(ceil_div(nxh, 128), d.ny, d.nz), fblock(128);
 
     cudaStream_t cs = nullptr;
     GBSW_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
@@ -325,14 +352,14 @@ gbsw_status PoissonSolver::build_graph()
         body = cp.conditional.phGraph_out[0];
         chk(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
         if (err == cudaSuccess) {
-            sor_sweep_kernel<true><<<sgrid, sblock, 0, cs>>>(d, 0, om, h2, e[0], e[1], r[0], p_hi);
-            sor_sweep_kernel<true><<<sgrid, sblock, 0, cs>>>(d, 1, om, h2, e[1], e[0], r[1], p_hi);
+            sor_sweep_kernel<true><<<sgrid, sblock, 0, cs>>>(d, 0, om, h2, e[0], e[1], r[0]);
+            sor_sweep_kernel<true><<<sgrid, sblock, 0, cs>>>(d, 1, om, h2, e[1], e[0], r[1]);
             for (int it = 1; it < m; ++it) {
-                sor_sweep_kernel<false><<<sgrid, sblock, 0, cs>>>(d, 0, om, h2, e[0], e[1], r[0], p_hi);
-                sor_sweep_kernel<false><<<sgrid, sblock, 0, cs>>>(d, 1, om, h2, e[1], e[0], r[1], p_hi);
+                sor_sweep_kernel<false><<<sgrid, sblock, 0, cs>>>(d, 0, om, h2, e[0], e[1], r[0]);
+                sor_sweep_kernel<false><<<sgrid, sblock, 0, cs>>>(d, 1, om, h2, e[1], e[0], r[1]);
             }
-            poisson_fold_kernel<<<fgrid, sblock, 0, cs>>>(d, 0, p_hi, e[0]);
-            poisson_fold_kernel<<<fgrid, sblock, 0, cs>>>(d, 1, p_hi, e[1]);
+            poisson_fold_kernel<<<fgrid, fblock, 0, cs>>>(d, 0, p_hi, e[0]);
+            poisson_fold_kernel<<<fgrid, fblock, 0, cs>>>(d, 1, p_hi, e[1]);
             poisson_resid_kernel<false><<<rgrid, POI_RED_THREADS, 0, cs>>>(d, b, p_hi, r[0], r[1], partials);
             poisson_test_kernel<true><<<1, POI_RED_THREADS, 0, cs>>>(partials, rblocks, ctl, tol, max_iter, m,
                                                                     1, handle);
@@ -366,23 +393,23 @@ gbsw_status PoissonSolver::enqueue_fixed(int niter)
     if (niter < 0) return GBSW_ERR_ARG;
     const size_t nc = (size_t)d.cplane * (size_t)(d.nz + 2);
     const float om = (float)omega, h2 = (float)(d.dx * d.dx);
-    const dim3 sgrid(ceil_div((d.nx + 1) / 2, 128), d.ny, ceil_div(d.nz, 2)), sblock(128);
-    const dim3 fgrid(ceil_div((d.nx + 1) / 2, 128), d.ny, d.nz);
+    const dim3 sgrid = sweep_grid(d), sblock(32, SOR_ROWS);
+    const dim3 fgrid(ceil_div((d.nx + 1) / 2, 128), d.ny, d.nz), fblock(128);
     GBSW_CUDA_TRY(cudaMemsetAsync(e[0], 0, nc * sizeof(float), stream));
     GBSW_CUDA_TRY(cudaMemsetAsync(e[1], 0, nc * sizeof(float), stream));
     poisson_resid_kernel<true><<<rgrid, POI_RED_THREADS, 0, stream>>>(d, b, p_hi, r[0], r[1], partials);
     poisson_test_kernel<false><<<1, POI_RED_THREADS, 0, stream>>>(partials, rblocks, ctl, 0.0, niter, 0, 0, 0);
     for (int it = 0; it < niter; ++it) {
         if (it == 0) {
-            sor_sweep_kernel<true><<<sgrid, sblock, 0, stream>>>(d, 0, om, h2, e[0], e[1], r[0], p_hi);
-            sor_sweep_kernel<true><<<sgrid, sblock, 0, stream>>>(d, 1, om, h2, e[1], e[0], r[1], p_hi);
+            sor_sweep_kernel<true><<<sgrid, sblock, 0, stream>>>(d, 0, om, h2, e[0], e[1], r[0]);
+            sor_sweep_kernel<true><<<sgrid, sblock, 0, stream>>>(d, 1, om, h2, e[1], e[0], r[1]);
         } else {
-            sor_sweep_kernel<false><<<sgrid, sblock, 0, stream>>>(d, 0, om, h2, e[0], e[1], r[0], p_hi);
-            sor_sweep_kernel<false><<<sgrid, sblock, 0, stream>>>(d, 1, om, h2, e[1], e[0], r[1], p_hi);
+            sor_sweep_kernel<false><<<sgrid, sblock, 0, stream>>>(d, 0, om, h2, e[0], e[1], r[0]);
+            sor_sweep_kernel<false><<<sgrid, sblock, 0, stream>>>(d, 1, om, h2, e[1], e[0], r[1]);
         }
     }
-    poisson_fold_kernel<<<fgrid, sblock, 0, stream>>>(d, 0, p_hi, e[0]);
-    poisson_fold_kernel<<<fgrid, sblock, 0, stream>>>(d, 1, p_hi, e[1]);
+    poisson_fold_kernel<<<fgrid, fblock, 0, stream>>>(d, 0, p_hi, e[0]);
+    poisson_fold_kernel<<<fgrid, fblock, 0, stream>>>(d, 1, p_hi, e[1]);
     poisson_resid_kernel<false><<<rgrid, POI_RED_THREADS, 0, stream>>>(d, b, p_hi, r[0], r[1], partials);
     poisson_test_kernel<false><<<1, POI_RED_THREADS, 0, stream>>>(partials, rblocks, ctl, 0.0, niter, niter,
                                                                    1, 0);

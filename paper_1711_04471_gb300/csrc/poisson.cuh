@@ -21,10 +21,12 @@
 // Device layout.  p_hi: (nz+2) x (ny+2) x pitch FP64, interior cell
 // (i,j,k) (1-based) at k*plane + j*pitch + i.  e and r are stored split by
 // colour c = (i+j+k) mod 2: colour array c holds cell (i,j,k) of that
-// colour at k*cplane + j*cpitch + 1 + ((i-1) >> 1), so a half-sweep reads
-// its own colour and the other colour with unit stride.  Slot 0 and the
-// slots past the last cell of a row, and the y/z ghost rows, stay 0: the
-// boundary rules enter only through d_c, and y is wrapped explicitly.
+// colour at k*cplane + j*cpitch + SOR_SLOT0 + ((i-1) >> 1), so a half-sweep
+// reads its own colour and the other colour with unit stride, and slot 0
+// of every row starts a 16-byte word group.  The SOR_SLOT0 words before
+// slot 0, the slots past the last cell of a row (at least four), and the
+// y/z ghost rows stay 0: the boundary rules enter only through d_c, and y
+// is wrapped explicitly.
 #pragma once
 
 #include "common.cuh"
@@ -34,7 +36,7 @@ namespace gbsw {
 struct PDims {
     int nx, ny, nz, pitch;
     long long plane;   // (ny+2) * pitch
-    int cpitch;        // row pitch of a colour array (>= (nx >> 1) + 2)
+    int cpitch;        // row pitch of a colour array: SOR_SLOT0 + round_up((nx+1)/2, 4) + 4
     long long cplane;  // (ny+2) * cpitch
     double dx;
 };
@@ -86,6 +88,9 @@ private:
 };
 
 constexpr int POI_RES_PLANES = 8;     // z-planes per thread of the residual kernel
+constexpr int SOR_SLOT0 = 4;          // offset of slot 0 in a colour row (keeps float4 groups aligned)
+constexpr int SOR_ROWS = 4;           // rows (warps) per block of the SOR sweep
+constexpr int SOR_KZ = 2;             // z-planes per thread of the SOR sweep
 constexpr int POI_RED_THREADS = 256;
 
 }  // namespace gbsw

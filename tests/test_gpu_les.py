@@ -70,6 +70,30 @@ def test_poisson_solve_matches_oracle_iterates(G):
     assert st == 0 and rr10 <= 1e-6 and it10 % 10 == 0 and it_o - 1 <= it10 < it_o + 11
 
 
+@pytest.mark.parametrize("shape", [(300, 16, 6), (257, 10, 5)])
+def test_poisson_fixed_iterations_match_oracle_on_wide_rows(G, shape):
+    """Rows wider than one block of the sweep and fold kernels (150 and 129
+    slots of a colour, the second an odd nx): 300 fixed iterations with a
+    fold and FP64 residual in between (check every 50) against the oracle's
+    iterates."""
+    import torch
+    nx, ny, nz = shape
+    dx = 4.0
+    rng = np.random.default_rng(nx)
+    b = rng.standard_normal((nz, ny, nx)).astype(np.float32)
+    P = ol.make_params(nx, ny, nz, dx=dx)
+    bo, po = ol.padded(P), ol.padded(P)
+    ol.interior(bo)[:] = b
+    ol.sor(P, bo, po, omega=1.8, tol=0.0, max_iter=300)
+    for tol in (-1.0, 1e-30):       # paper mode (direct launches) and the graph with its checks
+        pg = torch.zeros((nz, ny, nx), dtype=torch.float32, device="cuda")
+        st, it, rr = G.poisson_solve(pg, torch.from_numpy(b).cuda(), dx, omega=1.8, tol=tol, max_iter=300,
+                                     check_every=50)
+        assert it == 300
+        assert rel_l2(pg.cpu().numpy(), ol.interior(po)) <= 1e-5, tol
+        assert abs(rr - ol.residual(P, bo, po)) <= 1e-3 * rr
+
+
 def test_poisson_solve_reaches_fp64_accuracy(G):
     """The FP32 sweeps iterate on a correction of the FP64 pressure, so the
     residual keeps falling far below what FP32 storage of p alone allows."""

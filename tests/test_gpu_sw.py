@@ -65,6 +65,22 @@ def test_hump_1000_steps(SW, blocking):
     assert abs(vol[0] - v_or) / v_or < 1e-6
 
 
+def test_paper_setup_500(SW):
+    """The paper's 2DSW setup (Sec. 6.2, tests/golden/paper_setups.json):
+    dx = 1 m, dt = 0.01 s on its smallest grid, 500 x 500, 300 steps."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "paper_setups.json")) as f:
+        s = json.load(f)["sw2d"]
+    n = s["sizes"][0]
+    inp = inputs.sw_hump(n=n, dx=s["dx_m"], dt=s["dt_s"], sigma_cells=n / 20.0)
+    o, st, vol = run_both(SW, inp, 300)
+    assert rel_l2(st["eta"], o.eta_i) <= REL_L2
+    assert rel_l2(st["u"], o.u_f) <= REL_L2
+    assert rel_l2(st["v"], o.v_f) <= REL_L2
+    assert np.array_equal(st["wet"], o.wet_i)
+
+
 def test_lake_at_rest_bit_identical(SW):
     """Still water over wet/dry bathymetry stays bit-identical on the GPU too."""
     base = inputs.sw_wetdry(n=200, seed=7)

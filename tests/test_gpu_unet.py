@@ -98,3 +98,25 @@ def test_les_with_learned_warm_start_converges(U):
         assert np.linalg.norm(pa - pb) / np.linalg.norm(pa) < 1e-3
         warm.set_warm_start(None)
         assert warm.step(1)[0]["ms_guess"] < 0.05
+
+
+def test_trained_warm_start_saves_sor_iterations(U):
+    """The committed weights on the 256 x 256 x 128 workload (building seed
+    1003, which no training run used): from the same states, SOR started
+    from the network's guess reaches the same 1e-6 residual in clearly fewer
+    iterations than SOR started from the previous pressure."""
+    import os
+
+    from paper_1711_04471_gb300 import train_unet
+    weights = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                           "paper_1711_04471_gb300", "data", "unet_warmstart.npy")
+    with U.UNet(seed=0) as net:
+        net.set_params(np.load(weights))
+        rows = train_unet.compare_warm_starts(net, spinup=20, steps=3, spinup_tol=1e-4, log=lambda *a: None,
+                                              check_every=50, max_iter=400000)
+    for r in rows:
+        assert r["plain_res"] <= 1e-6 and r["nn_res"] <= 1e-6
+    plain = sum(r["plain_iters"] for r in rows)
+    nn = sum(r["nn_iters"] for r in rows)
+    print(f"SOR iterations over 3 steps: previous-pressure warm start {plain}, learned {nn}")
+    assert nn <= 0.8 * plain, (plain, nn)
