@@ -62,6 +62,17 @@ const char *gbsw_last_error(void);
  * Synchronous. */
 gbsw_status gbsw_selftest_wait(int which, long long budget);
 
+/* Self-test of the division by the Poisson operator's diagonal inside the
+ * SOR sweep (the paper has no counterpart): the sweep divides by
+ * d in {4, 5, 6, 7} through a rounded reciprocal and one FMA correction;
+ * this runs it on the device for every finite FP32 x and compares it bit
+ * for bit with the IEEE division x / d.  counts (host, 3 entries) receives
+ * the mismatches with |x| >= 2^-100, the mismatches with smaller |x|, and
+ * the smallest mismatching bit pattern (0xffffffff if none).  d outside
+ * 4..7 or a NULL counts gives GBSW_ERR_ARG.  Synchronous; about 4e9
+ * divisions. */
+gbsw_status gbsw_selftest_sor_division(int d, unsigned long long *counts);
+
 /* ------------------------------------------------------------------------
  * 2-D shallow water (Sec. 6.2: time loop of predictor "dyn", first-order
  * Shapiro filter "shapiro", then the velocity/state update).

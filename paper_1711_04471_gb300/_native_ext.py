@@ -52,5 +52,6 @@ def declare(L, sig):
     sig(L, "warm_start_features", C.c_int, [C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, vp, vp, vp, dp, vp])
     sig(L, "warm_start_apply", C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, vp, C.c_double, vp, vp])
     sig(L, "gbsw_selftest_wait", C.c_int, [C.c_int, C.c_longlong])
+    sig(L, "gbsw_selftest_sor_division", C.c_int, [C.c_int, C.POINTER(C.c_ulonglong)])
     sig(L, "poisson_solve", C.c_int, [C.c_int, C.c_int, C.c_int, C.c_double, vp, vp, C.c_double, C.c_double,
                                       C.c_int, C.c_int, vp, ip, dp])

@@ -29,61 +29,88 @@ __device__ __forceinline__ long long cidx(const PDims &d, int i, int j, int k)
     return (long long)k * d.cplane + (long long)j * d.cpitch + SOR_SLOT0 + ((i - 1) >> 1);
 }
 
-__device__ __forceinline__ float pdiag(const PDims &d, int i, int k)
-{
-    return 6.0f - (i == 1) - (k == 1) - (k == d.nz) + (i == d.nx);
-}
 
-// One colour half-sweep over cells with (i + j + k) % 2 == colour.  Thread
-// (g, j, kp) owns the cells of that colour at slots 4g .. 4g+3 of rows
-// (j, SOR_KZ kp + 1 .. SOR_KZ kp + SOR_KZ): every access of a plane is one
-// 16-byte vector (own correction, residual, the other colour's y and z
-// neighbours and its four x neighbours) plus one word (the fifth x
-// neighbour), so a warp covers 128 slots of a row with a few wide loads.
-// The per-cell arithmetic is that of the scalar update
+// One colour half-sweep over cells with (i + j + k) % 2 == colour.  A
+// thread owns the cells of that colour at slots s0 .. s0+3 of row j on
+// planes SOR_KZ blockIdx.z + 1 .. SOR_KZ blockIdx.z + SOR_KZ.  Rows of a
+// whole number of 32-group warps (FLAT = false): block = 32 groups of
+// SOR_THREADS / 32 consecutive rows, so a warp holds one row (its colour
+// parity q is warp-uniform).  Other rows (FLAT = true): thread t of a block
+// takes group t mod G of row t / G (G = groups per row), so no lane idles
+// at the end of a row; q may then differ inside a warp.
+// Every access of a plane is one 16-byte vector (own correction, residual,
+// the other colour's y and z neighbours and its four x neighbours) plus
+// one word (the fifth x neighbour, the other colour's slot s0 - 1 or
+// s0 + 4).  In-plane offsets are 32-bit (a colour plane holds fewer than
+// 2^31 words for every accepted size).
+// The per-cell arithmetic is the SOR update
 //   e <- e + omega ((sum of the six neighbours - dx^2 r) / d_c - e)
-// with the neighbour sum associated as (x pair + y pair) + z pair.
+// with the neighbour sum associated as (x pair + y pair) + z pair and the
+// division correctly rounded (sor_div).  d_c is 6 inside, 5 on the ground
+// and lid planes, one less at i = 1 and one more at i = nx (the entry
+// points require nx, nz >= 2).
 // Slots beyond the last cell of a row are pad words: they are written 0.
 // FIRST: first iteration after a residual check; the correction restarts
 // from 0 (the fold before the check has zeroed it), so the first red
 // half-sweep reads no neighbours and no old value.
-// Launch: grid (ceil(((nx+1)/2) / 128), ceil(ny / SOR_ROWS), ceil(nz / SOR_KZ)),
-// block (32, SOR_ROWS).
-template <bool FIRST>
-__global__ void __launch_bounds__(32 * SOR_ROWS)
-sor_sweep_kernel(PDims d, int colour, float omega, float h2, float *__restrict__ ec, const float *__restrict__ eo,
-                 const float *__restrict__ rc)
+// Launch: sweep_grid(d), block SOR_THREADS.
+template <bool FIRST, bool FLAT>
+__global__ void __launch_bounds__(SOR_THREADS)
+sor_sweep_kernel(PDims d, int colour, float omega, float h2, SorDiag dg, float *__restrict__ ec,
+                 const float *__restrict__ eo, const float *__restrict__ rc)
 {
-    const int s0 = 4 * (blockIdx.x * 32 + threadIdx.x);
-    const int j = blockIdx.y * SOR_ROWS + threadIdx.y + 1;
-    if (2 * s0 + 1 > d.nx || j > d.ny) return;  // no cell of either colour in this group
+    int j, s0;
+    if (FLAT) {
+        const int ngroups = ((d.nx + 1) / 2 + 3) >> 2;
+        const int t = blockIdx.x * SOR_THREADS + threadIdx.x;
+        j = t / ngroups + 1;
+        s0 = 4 * (t - (j - 1) * ngroups);
+        if (j > d.ny) return;
+    } else {
+        s0 = 4 * (blockIdx.x * 32 + (threadIdx.x & 31));
+        j = blockIdx.y * (SOR_THREADS / 32) + (threadIdx.x >> 5) + 1;
+        if (2 * s0 + 1 > d.nx || j > d.ny) return;  // no cell of either colour in this group
+    }
     const int jm = (j == 1) ? d.ny : j - 1;
     const int jp = (j == d.ny) ? 1 : j + 1;
     const bool need_nb = !FIRST || colour == 1;  // on the first red half-sweep every neighbour is still 0
-    const long long rowj = (long long)j * d.cpitch + SOR_SLOT0 + s0;
-    const long long dym = (long long)(jm - j) * d.cpitch, dyp = (long long)(jp - j) * d.cpitch;
+    const int o = j * d.cpitch + SOR_SLOT0 + s0;  // offset inside a colour plane
+    const int oym = o + (jm - j) * d.cpitch, oyp = o + (jp - j) * d.cpitch;
+    const int cpl = (int)d.cplane;
 #pragma unroll
     for (int h = 0; h < SOR_KZ; ++h) {
         const int k = SOR_KZ * blockIdx.z + 1 + h;
         if (k > d.nz) break;
         const int q = (colour + 1 + j + k) & 1;
-        const long long c = (long long)k * d.cplane + rowj;
-        const float4 e_old = FIRST ? make_float4(0.f, 0.f, 0.f, 0.f) : *reinterpret_cast<const float4 *>(ec + c);
-        const float4 r4 = *reinterpret_cast<const float4 *>(rc + c);
+        const size_t plane = (size_t)k * d.cplane;
+        float *__restrict__ ep = ec + plane;
+        const float *__restrict__ op = eo + plane;
+        // diagonal of this plane inside a row (index 1), at i = 1 (0) and at i = nx (2)
+        const bool mid = k != 1 && k != d.nz;
+        const float d_in = mid ? dg.d[2] : dg.d[1], y_in = mid ? dg.y[2] : dg.y[1];
+        const float d_lo = mid ? dg.d[1] : dg.d[0], y_lo = mid ? dg.y[1] : dg.y[0];
+        const float d_hi = mid ? dg.d[3] : dg.d[2], y_hi = mid ? dg.y[3] : dg.y[2];
+        const float4 e_old = FIRST ? make_float4(0.f, 0.f, 0.f, 0.f) : *reinterpret_cast<const float4 *>(ep + o);
+        const float4 r4 = *reinterpret_cast<const float4 *>(rc + plane + o);
         float sx[4] = {0.f, 0.f, 0.f, 0.f}, sy[4] = {0.f, 0.f, 0.f, 0.f}, sz[4] = {0.f, 0.f, 0.f, 0.f};
         if (need_nb) {
-            const float4 o = *reinterpret_cast<const float4 *>(eo + c);
-            const float4 ym = *reinterpret_cast<const float4 *>(eo + c + dym);
-            const float4 yp = *reinterpret_cast<const float4 *>(eo + c + dyp);
-            const float4 zm = *reinterpret_cast<const float4 *>(eo + c - d.cplane);
-            const float4 zp = *reinterpret_cast<const float4 *>(eo + c + d.cplane);
+            const float4 oc = *reinterpret_cast<const float4 *>(op + o);
+            const float4 zm = *reinterpret_cast<const float4 *>(op + o - cpl);
+            const float4 zp = *reinterpret_cast<const float4 *>(op + o + cpl);
+            const float4 ym = *reinterpret_cast<const float4 *>(op + oym);
+            const float4 yp = *reinterpret_cast<const float4 *>(op + oyp);
             // x neighbours of slot s are slots s - 1 + q and s + q of the other colour
-            if (q == 0) {
-                const float ol = eo[c - 1];
-                sx[0] = ol + o.x; sx[1] = o.x + o.y; sx[2] = o.y + o.z; sx[3] = o.z + o.w;
+            if (FLAT) {
+                const float xe = op[o + (q ? 4 : -1)];
+                const float w[6] = {xe, oc.x, oc.y, oc.z, oc.w, xe};
+#pragma unroll
+                for (int u = 0; u < 4; ++u) sx[u] = q ? w[u + 1] + w[u + 2] : w[u] + w[u + 1];
+            } else if (q == 0) {
+                const float ol = op[o - 1];
+                sx[0] = ol + oc.x; sx[1] = oc.x + oc.y; sx[2] = oc.y + oc.z; sx[3] = oc.z + oc.w;
             } else {
-                const float orr = eo[c + 4];
-                sx[0] = o.x + o.y; sx[1] = o.y + o.z; sx[2] = o.z + o.w; sx[3] = o.w + orr;
+                const float orr = op[o + 4];
+                sx[0] = oc.x + oc.y; sx[1] = oc.y + oc.z; sx[2] = oc.z + oc.w; sx[3] = oc.w + orr;
             }
             sy[0] = ym.x + yp.x; sy[1] = ym.y + yp.y; sy[2] = ym.z + yp.z; sy[3] = ym.w + yp.w;
             sz[0] = zm.x + zp.x; sz[1] = zm.y + zp.y; sz[2] = zm.z + zp.z; sz[3] = zm.w + zp.w;
@@ -92,12 +119,14 @@ sor_sweep_kernel(PDims d, int colour, float omega, float h2, float *__restrict__
         const float rr4[4] = {r4.x, r4.y, r4.z, r4.w};
         float u[4];
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            const int i = 2 * (s0 + t) + 1 + q;
-            const float s = need_nb ? (sx[t] + sy[t]) + sz[t] : 0.0f;
-            u[t] = i <= d.nx ? eo4[t] + omega * ((s - h2 * rr4[t]) / pdiag(d, i, k) - eo4[t]) : 0.0f;
+        for (int tt = 0; tt < 4; ++tt) {
+            const int i = 2 * (s0 + tt) + 1 + q;
+            const float s = need_nb ? (sx[tt] + sy[tt]) + sz[tt] : 0.0f;
+            const float dc = i == 1 ? d_lo : (i == d.nx ? d_hi : d_in);
+            const float yc = i == 1 ? y_lo : (i == d.nx ? y_hi : y_in);
+            u[tt] = i <= d.nx ? eo4[tt] + omega * (sor_div(s - h2 * rr4[tt], dc, yc) - eo4[tt]) : 0.0f;
         }
-        *reinterpret_cast<float4 *>(ec + c) = make_float4(u[0], u[1], u[2], u[3]);
+        *reinterpret_cast<float4 *>(ep + o) = make_float4(u[0], u[1], u[2], u[3]);
     }
 }
 
@@ -226,11 +255,31 @@ __global__ void poisson_gather_kernel(PDims d, const double *__restrict__ src, f
 
 // ---------------------------------------------------------------------------
 
-// Grid of sor_sweep_kernel: 128 slots (32 threads x 4) by SOR_ROWS rows by
-// SOR_KZ planes per block.
+// Launch shape of sor_sweep_kernel: the warp-per-row mapping when a row
+// holds a whole number of 32-group warps, else the flat one.
+static bool sweep_flat(const PDims &d)
+{
+    return ((((d.nx + 1) / 2) + 3) / 4) % 32 != 0;
+}
+
 static dim3 sweep_grid(const PDims &d)
 {
-    return dim3(ceil_div((d.nx + 1) / 2, 128), ceil_div(d.ny, SOR_ROWS), ceil_div(d.nz, SOR_KZ));
+    const long long ngroups = (((d.nx + 1) / 2) + 3) / 4;
+    if (sweep_flat(d)) return dim3(ceil_div(ngroups * d.ny, SOR_THREADS), 1, ceil_div(d.nz, SOR_KZ));
+    return dim3(ceil_div(ngroups, 32), ceil_div(d.ny, SOR_THREADS / 32), ceil_div(d.nz, SOR_KZ));
+}
+
+// Enqueue one colour half-sweep.
+template <bool FIRST>
+static void launch_sweep(const PDims &d, int colour, float om, float h2, float *ec, const float *eo, const float *rc,
+                         cudaStream_t s)
+{
+    const dim3 g = sweep_grid(d);
+    const SorDiag dg = sor_diag();
+    if (sweep_flat(d))
+        sor_sweep_kernel<FIRST, true><<<g, SOR_THREADS, 0, s>>>(d, colour, om, h2, dg, ec, eo, rc);
+    else
+        sor_sweep_kernel<FIRST, false><<<g, SOR_THREADS, 0, s>>>(d, colour, om, h2, dg, ec, eo, rc);
 }
 
 gbsw_status PoissonSolver::init(int nx, int ny, int nz, double dx, const float *b_dev, cudaStream_t s)
@@ -305,7 +354,6 @@ gbsw_status PoissonSolver::build_graph()
     const size_t nc = (size_t)d.cplane * (size_t)(d.nz + 2);
     const float om = (float)omega, h2 = (float)(d.dx * d.dx);
     const int nxh = (d.nx + 1) / 2;
-    const dim3 sgrid = sweep_grid(d), sblock(32, SOR_ROWS);
     const dim3 fgrid(ceil_div(nxh, 128), d.ny, d.nz), fblock(128);
 
     cudaStream_t cs = nullptr;
@@ -352,11 +400,11 @@ gbsw_status PoissonSolver::build_graph()
         body = cp.conditional.phGraph_out[0];
         chk(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
         if (err == cudaSuccess) {
-            sor_sweep_kernel<true><<<sgrid, sblock, 0, cs>>>(d, 0, om, h2, e[0], e[1], r[0]);
-            sor_sweep_kernel<true><<<sgrid, sblock, 0, cs>>>(d, 1, om, h2, e[1], e[0], r[1]);
+            launch_sweep<true>(d, 0, om, h2, e[0], e[1], r[0], cs);
+            launch_sweep<true>(d, 1, om, h2, e[1], e[0], r[1], cs);
             for (int it = 1; it < m; ++it) {
-                sor_sweep_kernel<false><<<sgrid, sblock, 0, cs>>>(d, 0, om, h2, e[0], e[1], r[0]);
-                sor_sweep_kernel<false><<<sgrid, sblock, 0, cs>>>(d, 1, om, h2, e[1], e[0], r[1]);
+                launch_sweep<false>(d, 0, om, h2, e[0], e[1], r[0], cs);
+                launch_sweep<false>(d, 1, om, h2, e[1], e[0], r[1], cs);
             }
             poisson_fold_kernel<<<fgrid, fblock, 0, cs>>>(d, 0, p_hi, e[0]);
             poisson_fold_kernel<<<fgrid, fblock, 0, cs>>>(d, 1, p_hi, e[1]);
@@ -393,7 +441,6 @@ gbsw_status PoissonSolver::enqueue_fixed(int niter)
     if (niter < 0) return GBSW_ERR_ARG;
     const size_t nc = (size_t)d.cplane * (size_t)(d.nz + 2);
     const float om = (float)omega, h2 = (float)(d.dx * d.dx);
-    const dim3 sgrid = sweep_grid(d), sblock(32, SOR_ROWS);
     const dim3 fgrid(ceil_div((d.nx + 1) / 2, 128), d.ny, d.nz), fblock(128);
     GBSW_CUDA_TRY(cudaMemsetAsync(e[0], 0, nc * sizeof(float), stream));
     GBSW_CUDA_TRY(cudaMemsetAsync(e[1], 0, nc * sizeof(float), stream));
@@ -401,11 +448,11 @@ gbsw_status PoissonSolver::enqueue_fixed(int niter)
     poisson_test_kernel<false><<<1, POI_RED_THREADS, 0, stream>>>(partials, rblocks, ctl, 0.0, niter, 0, 0, 0);
     for (int it = 0; it < niter; ++it) {
         if (it == 0) {
-            sor_sweep_kernel<true><<<sgrid, sblock, 0, stream>>>(d, 0, om, h2, e[0], e[1], r[0]);
-            sor_sweep_kernel<true><<<sgrid, sblock, 0, stream>>>(d, 1, om, h2, e[1], e[0], r[1]);
+            launch_sweep<true>(d, 0, om, h2, e[0], e[1], r[0], stream);
+            launch_sweep<true>(d, 1, om, h2, e[1], e[0], r[1], stream);
         } else {
-            sor_sweep_kernel<false><<<sgrid, sblock, 0, stream>>>(d, 0, om, h2, e[0], e[1], r[0]);
-            sor_sweep_kernel<false><<<sgrid, sblock, 0, stream>>>(d, 1, om, h2, e[1], e[0], r[1]);
+            launch_sweep<false>(d, 0, om, h2, e[0], e[1], r[0], stream);
+            launch_sweep<false>(d, 1, om, h2, e[1], e[0], r[1], stream);
         }
     }
     poisson_fold_kernel<<<fgrid, fblock, 0, stream>>>(d, 0, p_hi, e[0]);

@@ -89,8 +89,41 @@ private:
 
 constexpr int POI_RES_PLANES = 8;     // z-planes per thread of the residual kernel
 constexpr int SOR_SLOT0 = 4;          // offset of slot 0 in a colour row (keeps float4 groups aligned)
-constexpr int SOR_ROWS = 4;           // rows (warps) per block of the SOR sweep
+constexpr int SOR_THREADS = 128;      // threads per block of the SOR sweep
 constexpr int SOR_KZ = 2;             // z-planes per thread of the SOR sweep
 constexpr int POI_RED_THREADS = 256;
+
+// The values 4, 5, 6, 7 that the diagonal d_c takes, and their reciprocals
+// rounded to FP32 (y = RN(1/d), formed by an IEEE division on the host).
+struct SorDiag {
+    float d[4];
+    float y[4];
+};
+
+inline SorDiag sor_diag()
+{
+    SorDiag g;
+    for (int n = 0; n < 4; ++n) {
+        g.d[n] = (float)(4 + n);
+        g.y[n] = 1.0f / g.d[n];
+    }
+    return g;
+}
+
+// x / d rounded to nearest even, for d in {4, 5, 6, 7} and y = RN(1/d):
+// q = RN(x y) is within one unit in the last place of x / d, the remainder
+// x - q d is then exact in one FMA, and q + (x - q d) y rounded once is the
+// correctly rounded quotient (the correction step of P. Markstein, "IA-64
+// and Elementary Functions", Prentice Hall 2000, ch. 8).  When the
+// remainder is zero, q is the quotient as it stands (this keeps the sign
+// of a zero x).  A non-finite x gives a NaN (the residual check reports
+// it).  gbsw_selftest_sor_division compares it with the IEEE division for
+// every finite FP32 x.
+__device__ __forceinline__ float sor_div(float x, float d, float y)
+{
+    const float q = __fmul_rn(x, y);
+    const float r = __fmaf_rn(-q, d, x);
+    return r == 0.0f ? q : __fmaf_rn(r, y, q);
+}
 
 }  // namespace gbsw

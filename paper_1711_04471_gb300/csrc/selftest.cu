@@ -1,8 +1,12 @@
-// Self-test of the bounded device-side waits: each kernel waits for
+// Self-tests.
+// gbsw_selftest_wait: the bounded device-side waits.  Each kernel waits for
 // something that never happens (an mbarrier phase nobody completes, a flag
 // nobody sets) with a short budget, and must give up, record
 // GBSW_ERR_TIMEOUT and return, leaving the context usable.
+// gbsw_selftest_sor_division: the SOR sweep's division by the diagonal
+// (sor_div) against the IEEE division x / d for every finite FP32 x.
 #include "common.cuh"
+#include "poisson.cuh"
 #include "tc.cuh"
 
 namespace {
@@ -31,7 +35,51 @@ __global__ void selftest_flag_kernel(const unsigned *flag, long long spins, int 
     }
 }
 
+// Every 32-bit pattern once (grid-stride); out[0] counts mismatches with a
+// normal x of magnitude at least 2^-100, out[1] the others; out[2] is the
+// smallest mismatching pattern (0xffffffff if none).
+__global__ void selftest_div_kernel(float d, float y, unsigned long long *out)
+{
+    unsigned long long bad_normal = 0, bad_tiny = 0;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long b = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; b < (1ull << 32);
+         b += stride) {
+        const float x = __uint_as_float((unsigned)b);
+        if (!isfinite(x)) continue;
+        const float got = gbsw::sor_div(x, d, y);
+        const float want = x / d;
+        if (__float_as_uint(got) != __float_as_uint(want)) {
+            if (fabsf(x) >= 0x1p-100f) ++bad_normal;
+            else ++bad_tiny;
+            atomicMin(&out[2], b);
+        }
+    }
+    if (bad_normal) atomicAdd(&out[0], bad_normal);
+    if (bad_tiny) atomicAdd(&out[1], bad_tiny);
+}
+
 }  // namespace
+
+extern "C" gbsw_status gbsw_selftest_sor_division(int d, unsigned long long *counts)
+{
+    if (d < 4 || d > 7 || !counts) return GBSW_ERR_ARG;
+    const gbsw::SorDiag dg = gbsw::sor_diag();
+    unsigned long long *dev = nullptr;
+    GBSW_CUDA_TRY(cudaMalloc((void **)&dev, 3 * sizeof(unsigned long long)));
+    unsigned long long init[3] = {0, 0, 0xffffffffull};
+    cudaError_t e = cudaMemcpy(dev, init, sizeof(init), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        selftest_div_kernel<<<4 * gbsw::sm_count(), 256>>>(dg.d[d - 4], dg.y[d - 4], dev);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(counts, dev, sizeof(init), cudaMemcpyDeviceToHost);
+    cudaFree(dev);
+    if (e != cudaSuccess) {
+        gbsw::record_cuda_error(e, "gbsw_selftest_sor_division", __FILE__, __LINE__);
+        return GBSW_ERR_CUDA;
+    }
+    return GBSW_OK;
+}
 
 extern "C" gbsw_status gbsw_selftest_wait(int which, long long budget)
 {

@@ -46,3 +46,23 @@ def test_solver_reports_not_converged_and_nonfinite_rhs(lib):
     with pytest.raises(GBSWError) as e:
         poisson_solve(torch.zeros_like(b), b, 4.0, tol=1e-6, max_iter=10, check_every=5)
     assert e.value.status == -5
+
+
+@pytest.mark.parametrize("d", [4, 5, 6, 7])
+def test_sor_division_is_correctly_rounded(lib, d):
+    """The sweep's division by the diagonal (rounded reciprocal plus one FMA
+    correction) equals the IEEE division x / d bit for bit for every finite
+    FP32 x of magnitude at least 2^-100 (SOR values never get near that)."""
+    import ctypes as C
+    counts = (C.c_ulonglong * 3)()
+    assert lib.gbsw_selftest_sor_division(d, counts) == 0
+    print(f"d = {d}: {counts[0]} mismatches for |x| >= 2^-100, {counts[1]} below, first {counts[2]:#x}")
+    assert counts[0] == 0, (counts[0], hex(counts[2]))
+
+
+def test_sor_division_selftest_rejects_bad_arguments(lib):
+    import ctypes as C
+    counts = (C.c_ulonglong * 3)()
+    assert lib.gbsw_selftest_sor_division(3, counts) == -1
+    assert lib.gbsw_selftest_sor_division(8, counts) == -1
+    assert lib.gbsw_selftest_sor_division(6, None) == -1
