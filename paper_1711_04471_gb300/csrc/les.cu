@@ -514,7 +514,7 @@ gbsw_status les_step(gbsw_les *s, int nsteps, gbsw_les_stats *stats)
             if (st != GBSW_OK) break;
         }
         if (stats) cudaEventRecord(ev[4 * t + 2], s->stream);
-        st = s->fixed_iters > 0 ? s->solver.enqueue_fixed(s->fixed_iters) : s->solver.enqueue();
+        st = s->fixed_iters > 0 ? s->solver.enqueue_fixed(s->fixed_iters, true) : s->solver.enqueue();
         if (st != GBSW_OK) break;
         if (stats) cudaEventRecord(ev[4 * t + 3], s->stream);
         st = s->solver.record(s->ctl_log + t);

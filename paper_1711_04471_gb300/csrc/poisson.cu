@@ -317,8 +317,10 @@ void PoissonSolver::release()
 {
     if (exec_) cudaGraphExecDestroy(exec_);
     if (graph_) cudaGraphDestroy(graph_);
+    if (fixed_exec_) cudaGraphExecDestroy(fixed_exec_);
     exec_ = nullptr;
     graph_ = nullptr;
+    fixed_exec_ = nullptr;
     cudaFree(p_hi);
     for (int c = 0; c < 2; ++c) {
         cudaFree(e[c]);
@@ -337,6 +339,7 @@ gbsw_status PoissonSolver::configure(double omega_, double tol_, int max_iter_, 
     if (!(omega_ > 0.0 && omega_ < 2.0) || !(tol_ >= 0.0) || max_iter_ < 0 || check_every < 1 || check_every > 1000)
         return GBSW_ERR_ARG;
     if (omega_ != omega || tol_ != tol || max_iter_ != max_iter || check_every != m) dirty_ = true;
+    if (omega_ != omega) fixed_dirty_ = true;
     omega = omega_;
     tol = tol_;
     max_iter = max_iter_;
@@ -436,9 +439,39 @@ gbsw_status PoissonSolver::enqueue()
     return GBSW_OK;
 }
 
-gbsw_status PoissonSolver::enqueue_fixed(int niter)
+gbsw_status PoissonSolver::enqueue_fixed(int niter, bool use_graph)
 {
     if (niter < 0) return GBSW_ERR_ARG;
+    if (!use_graph || niter > SOR_FIXED_GRAPH_MAX_ITER) return record_fixed(niter, stream);
+    if (!fixed_exec_ || fixed_niter_ != niter || fixed_dirty_) {
+        if (fixed_exec_) cudaGraphExecDestroy(fixed_exec_);
+        fixed_exec_ = nullptr;
+        cudaStream_t cs = nullptr;
+        GBSW_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t g = nullptr;
+        gbsw_status st = GBSW_OK;
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            st = record_fixed(niter, cs);
+            e = cudaStreamEndCapture(cs, &g);
+        }
+        if (e == cudaSuccess && st == GBSW_OK) e = cudaGraphInstantiate(&fixed_exec_, g, 0);
+        if (g) cudaGraphDestroy(g);
+        cudaStreamDestroy(cs);
+        if (e != cudaSuccess || st != GBSW_OK) {
+            if (e != cudaSuccess) record_cuda_error(e, "poisson fixed-count graph", __FILE__, __LINE__);
+            fixed_exec_ = nullptr;
+            return st != GBSW_OK ? st : GBSW_ERR_CUDA;
+        }
+        fixed_niter_ = niter;
+        fixed_dirty_ = false;
+    }
+    GBSW_CUDA_TRY(cudaGraphLaunch(fixed_exec_, stream));
+    return GBSW_OK;
+}
+
+gbsw_status PoissonSolver::record_fixed(int niter, cudaStream_t stream)
+{
     const size_t nc = (size_t)d.cplane * (size_t)(d.nz + 2);
     const float om = (float)omega, h2 = (float)(d.dx * d.dx);
     const dim3 fgrid(ceil_div((d.nx + 1) / 2, 128), d.ny, d.nz), fblock(128);
@@ -513,7 +546,7 @@ extern "C" gbsw_status poisson_solve(int nx, int ny, int nz, double dx, float *p
             st = GBSW_ERR_CUDA;
             break;
         }
-        st = fixed ? S.enqueue_fixed(max_iter) : S.enqueue();
+        st = fixed ? S.enqueue_fixed(max_iter, false) : S.enqueue();
         if (st != GBSW_OK) break;
         poisson_gather_kernel<<<g, blk, 0, s>>>(S.d, S.p_hi, p);
         if ((e = cudaGetLastError()) != cudaSuccess ||

@@ -61,9 +61,11 @@ public:
     // Enqueue one solve (asynchronous; one graph launch).
     gbsw_status enqueue();
     // Enqueue exactly niter iterations with no convergence test (the
-    // paper's fixed-count SOR), launched directly on the stream; the control
-    // block receives the final residual.
-    gbsw_status enqueue_fixed(int niter);
+    // paper's fixed-count SOR); the control block receives the final
+    // residual.  With use_graph (a solver that is used again) and niter up
+    // to SOR_FIXED_GRAPH_MAX_ITER, the sequence is captured once into a
+    // CUDA graph and replayed; otherwise its kernels are launched directly.
+    gbsw_status enqueue_fixed(int niter, bool use_graph);
     // Copy the control block of the last solve into *out (device -> device).
     gbsw_status record(PoissonCtl *dev_dst);
 
@@ -82,6 +84,10 @@ public:
 
 private:
     gbsw_status build_graph();
+    gbsw_status record_fixed(int niter, cudaStream_t s);
+    cudaGraphExec_t fixed_exec_ = nullptr;
+    int fixed_niter_ = -1;
+    bool fixed_dirty_ = true;
     cudaGraph_t graph_ = nullptr;
     cudaGraphExec_t exec_ = nullptr;
     bool dirty_ = true;
@@ -91,6 +97,7 @@ constexpr int POI_RES_PLANES = 8;     // z-planes per thread of the residual ker
 constexpr int SOR_SLOT0 = 4;          // offset of slot 0 in a colour row (keeps float4 groups aligned)
 constexpr int SOR_THREADS = 128;      // threads per block of the SOR sweep
 constexpr int SOR_KZ = 2;             // z-planes per thread of the SOR sweep
+constexpr int SOR_FIXED_GRAPH_MAX_ITER = 1000;   // longest fixed-count solve captured into a graph
 constexpr int POI_RED_THREADS = 256;
 
 // The values 4, 5, 6, 7 that the diagonal d_c takes, and their reciprocals

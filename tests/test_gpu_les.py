@@ -70,12 +70,13 @@ def test_poisson_solve_matches_oracle_iterates(G):
     assert st == 0 and rr10 <= 1e-6 and it10 % 10 == 0 and it_o - 1 <= it10 < it_o + 11
 
 
-@pytest.mark.parametrize("shape", [(300, 16, 6), (257, 10, 5)])
+@pytest.mark.parametrize("shape", [(300, 16, 6), (257, 10, 5), (256, 6, 4), (512, 4, 2)])
 def test_poisson_fixed_iterations_match_oracle_on_wide_rows(G, shape):
-    """Rows wider than one block of the sweep and fold kernels (150 and 129
-    slots of a colour, the second an odd nx): 300 fixed iterations with a
-    fold and FP64 residual in between (check every 50) against the oracle's
-    iterates."""
+    """Rows wider than one block of the sweep and fold kernels: 150 and 129
+    slots of a colour (the second an odd nx; both take the flat thread
+    mapping), and 128 and 256 slots (one and two warps per row, the
+    warp-per-row mapping).  300 fixed iterations with a fold and FP64
+    residual in between (check every 50) against the oracle's iterates."""
     import torch
     nx, ny, nz = shape
     dx = 4.0
@@ -133,6 +134,26 @@ def _gpu_from_oracle(G, s, nx, ny, nz, solid, **kw):
     g.set("p", s.p)
     g.step_count = s.step_count
     return g
+
+
+def test_fixed_iteration_steps_match_oracle(G):
+    """The paper's mode (les_set_fixed_iterations, 50 SOR iterations per
+    step): two steps from rest, the second replaying the cached graph of the
+    fixed-count solve, against the oracle stepping with exactly 50
+    iterations (tolerance 0)."""
+    nx, ny, nz, solid = small_case()
+    P = ol.make_params(nx, ny, nz, tol=0.0, max_iter=50)
+    s = ol.LESState(P, solid)
+    with G.LES(nx, ny, nz, solid) as g:
+        g.set_fixed_iterations(50)
+        for step in range(2):
+            st = g.step(1)[0]
+            s.step(1)
+            it_o, rr_o, _ = s.history[-1]
+            assert st["iters"] == it_o == 50
+            assert rel_l2(g.get("u"), s.u, INT) <= REL, step
+            assert rel_l2(g.get("p"), s.p, INT) <= REL, step
+            assert abs(st["rel_res"] - rr_o) <= 1e-3 * rr_o, step
 
 
 @pytest.mark.parametrize("warm", [0, 3])
