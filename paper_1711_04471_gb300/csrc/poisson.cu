@@ -133,18 +133,18 @@ sor_sweep_kernel(PDims d, int colour, float omega, float h2, SorDiag dg, float *
 // r = b - A p_hi in FP64 (the correction has been folded into p_hi; r is
 // stored as FP32 in the colour arrays), with block partial sums of ||r||^2
 // and, with WITH_BB (once per solve), of ||b||^2.  Block (bx, j, bz): 256
-// cells of row j from i = 256 bx + 1, planes 8 bz + 1 .. 8 bz + 8 (no index
-// division).  A p_hi = (sum of neighbours - d_c p) / dx^2 with
-// d_c = 6 - [i == 1] - [k == 1] - [k == nz] + [i == nx] is formed as
-// sum - 6 p plus the boundary terms, so that interior cells take 6 FP64
-// additions and one FMA.
+// cells of row j from i = 256 bx + 1, planes POI_RES_PLANES bz + 1 ..
+// (no index division).  A p_hi = (sum of neighbours - d_c p) / dx^2 with
+// d_c = 6 - [i == 1] - [k == 1] - [k == nz] + [i == nx]: five FP64
+// additions and one FMA per cell.  The kernel is bound by the FP64 pipe,
+// so 1/dx^2 comes from the host and d_c from integer selects.
 template <bool WITH_BB>
 __global__ void __launch_bounds__(POI_RED_THREADS)
 poisson_resid_kernel(PDims d, const float *__restrict__ b, const double *__restrict__ p_hi, float *__restrict__ r0,
                      float *__restrict__ r1, double *__restrict__ partials)
 {
     __shared__ double red[POI_RED_THREADS / 32];
-    const double r2 = 1.0 / (d.dx * d.dx);
+    const double r2 = d.rdx2;
     const int i = blockIdx.x * POI_RED_THREADS + threadIdx.x + 1;
     const int j = blockIdx.y + 1;
     const int jm = (j == 1) ? d.ny : j - 1;
@@ -162,11 +162,11 @@ poisson_resid_kernel(PDims d, const float *__restrict__ b, const double *__restr
             const double pc = p_hi[pidx(d, i, j, k)];
             const double nb = (P(i - 1, j, k) + P(i + 1, j, k)) + (P(i, jm, k) + P(i, jp, k)) +
                               (P(i, j, k - 1) + P(i, j, k + 1));
-            double s = fma(-6.0, pc, nb);
-            if (i == 1) s += pc;
-            if (k == 1) s += pc;
-            if (k == d.nz) s += pc;
-            if (i == d.nx) s -= pc;
+            // d_c = 6 - [i == 1] - [k == 1] - [k == nz] + [i == nx] in {4, .., 7}
+            // (nx, nz >= 2), picked by integer selects: no FP64 operation
+            const int dci = 6 - (i == 1) - (k == 1) - (k == d.nz) + (i == d.nx);
+            const double dc = dci == 6 ? 6.0 : (dci == 5 ? 5.0 : (dci == 7 ? 7.0 : 4.0));
+            const double s = fma(-dc, pc, nb);
             const double bc = (double)b[pidx(d, i, j, k)];
             const double res = fma(-s, r2, bc);
             float *ra = ((i + j + k) & 1) ? r1 : r0;
@@ -292,6 +292,7 @@ gbsw_status PoissonSolver::init(int nx, int ny, int nz, double dx, const float *
     d.cpitch = SOR_SLOT0 + (int)round_up((size_t)(nx + 1) / 2, 4) + 4;
     d.cplane = (long long)(ny + 2) * d.cpitch;
     d.dx = dx;
+    d.rdx2 = 1.0 / (dx * dx);
     b = b_dev;
     stream = s;
     const size_t n = (size_t)d.plane * (size_t)(nz + 2);

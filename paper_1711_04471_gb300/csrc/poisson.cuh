@@ -39,6 +39,7 @@ struct PDims {
     int cpitch;        // row pitch of a colour array: SOR_SLOT0 + round_up((nx+1)/2, 4) + 4
     long long cplane;  // (ny+2) * cpitch
     double dx;
+    double rdx2;       // 1 / dx^2, formed once on the host (an FP64 division per thread costs dozens of FP64 operations)
 };
 
 struct PoissonCtl {
@@ -93,7 +94,7 @@ private:
     bool dirty_ = true;
 };
 
-constexpr int POI_RES_PLANES = 8;     // z-planes per thread of the residual kernel
+constexpr int POI_RES_PLANES = 16;    // z-planes per thread of the residual kernel
 constexpr int SOR_SLOT0 = 4;          // offset of slot 0 in a colour row (keeps float4 groups aligned)
 constexpr int SOR_THREADS = 128;      // threads per block of the SOR sweep
 constexpr int SOR_KZ = 2;             // z-planes per thread of the SOR sweep
