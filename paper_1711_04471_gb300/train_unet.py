@@ -228,7 +228,7 @@ def main():
     ap.add_argument("--factor", type=int, default=16)
     ap.add_argument("--data", help="load the solved pairs from this .npz instead of running the LES")
     ap.add_argument("--save-data", help="write the solved pairs to this .npz")
-    ap.add_argument("--iters", type=int, default=20000)
+    ap.add_argument("--iters", type=int, default=60000)
     ap.add_argument("--batch", type=int, default=32)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--init-seed", type=int, default=0)
