@@ -119,4 +119,4 @@ def test_trained_warm_start_saves_sor_iterations(U):
     plain = sum(r["plain_iters"] for r in rows)
     nn = sum(r["nn_iters"] for r in rows)
     print(f"SOR iterations over 3 steps: previous-pressure warm start {plain}, learned {nn}")
-    assert nn <= 0.8 * plain, (plain, nn)
+    assert nn <= 0.6 * plain, (plain, nn)
