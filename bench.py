@@ -490,6 +490,44 @@ def run_sw_paper(args, rank, world, local):
                       "sizes": res}), flush=True)
 
 
+def run_sw64(args, rank, world, local):
+    """The FP64 variant of the 2DSW step (three kernels per step, every
+    operation rounded as written) on the 4096^2 wet/dry grid: 100 time
+    steps plus the FP64 volume per bench step."""
+    import torch
+
+    import paper_1711_04471_gb300 as P
+    from paper_1711_04471_gb300 import inputs
+    from paper_1711_04471_gb300.sw import SW64
+    P.build()
+    torch.cuda.set_device(local)
+    inp = inputs.sw_wetdry(n=N_CELLS_SIDE, seed=1001)
+    cells = N_CELLS_SIDE * N_CELLS_SIDE
+    with SW64(inp.params(), inp.H, inp.eta0, stream=torch.cuda.current_stream()) as g:
+        for _ in range(args.warmup):
+            g.step(STEPS_PER_BENCH_STEP)
+            g.volume()
+        clocks = ClockSampler(torch.cuda.current_device())
+        clocks.start()
+        t = _timed_region(lambda: [(g.step(STEPS_PER_BENCH_STEP), g.volume()) for _ in range(args.steps)], world)
+        clk = clocks.stop()
+    if rank != 0:
+        return
+    value = cells * STEPS_PER_BENCH_STEP * args.steps * world / t
+    peak, peak_kind = _peaks()
+    ach = 120.0 * cells * STEPS_PER_BENCH_STEP * args.steps / t / 1e9
+    print(json.dumps({"metric": "cell-updates/s (FP64 2DSW)", "value": value, "unit": "cell-updates/s", "n_gpus": world,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3,
+                      "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                      "data": "synthetic",
+                      "config": {"workload": "2DSW 4096x4096 wet/dry, FP64 end to end (3 kernels per time step), "
+                                             "100 time steps + FP64 volume per step"},
+                      "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                                   "traffic": None, "peak_kind": peak_kind, "kernel": "sw64 momentum/continuity/shapiro",
+                                   "per_unit": "120 B per cell-update (48 + 40 + 32 B over the three kernels)"},
+                      "clocks": clk}), flush=True)
+
+
 def run_les_paper(args, rank, world, local):
     """The paper's UFLES setup (Sec. 6.3.2): 300x300x90 cells, 50 SOR
     iterations per step, dt = 0.025 s over 1.2 km; per-phase device times."""
@@ -528,7 +566,8 @@ def run_les_paper(args, rank, world, local):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="sw4096", choices=["sw4096", "ensemble", "les", "les-nn", "sw-paper", "les-paper"])
+    ap.add_argument("--workload", default="sw4096", choices=["sw4096", "sw64", "ensemble", "les", "les-nn", "sw-paper",
+                                                                 "les-paper"])
     ap.add_argument("--spinup", type=int, default=20)
     ap.add_argument("--weights", default=os.path.join(ROOT, "paper_1711_04471_gb300", "data", "unet_warmstart.npy"))
     ap.add_argument("--gpus", type=int, default=1)
@@ -550,6 +589,8 @@ def main():
         run_reference(args, rank, world)
     elif args.workload == "ensemble":
         run_ensemble(args, rank, world, local)
+    elif args.workload == "sw64":
+        run_sw64(args, rank, world, local)
     elif args.workload == "sw-paper":
         run_sw_paper(args, rank, world, local)
     elif args.workload == "les-paper":

@@ -143,6 +143,40 @@ gbsw_status sw_set_blocking(gbsw_sw *sw, int steps_per_launch);
 void sw_destroy(gbsw_sw *sw);
 
 /* ------------------------------------------------------------------------
+ * 2DSW in FP64 end to end (Sec. 6.2: the time loop of "dyn" and "shapiro",
+ * which the paper's compiler turns into three map kernels; the paper does
+ * not state the precision).  The same method, parameters and conventions
+ * as sw_* above, run as three kernels per step (momentum on the faces,
+ * continuity on the cells, masked Shapiro filter) with every FP64
+ * operation in the order written in the formulas above and rounded as
+ * written (no multiply-add contraction), so the state is a deterministic
+ * function of the inputs.  Slower than sw_step (FP64 throughput and no
+ * temporal blocking); meant for precision studies.
+ * ---------------------------------------------------------------------- */
+
+typedef struct gbsw_sw64 gbsw_sw64;
+
+/* As sw_create (same arguments, checks and errors), keeping H, eta, u, v
+ * in FP64 on the device. */
+gbsw_status sw64_create(const gbsw_sw_params *params, const double *H, const double *eta0,
+                        void *stream, gbsw_sw64 **out);
+
+/* Advance by nsteps >= 0 time steps (3 kernel launches per step,
+ * asynchronous on the context stream). */
+gbsw_status sw64_step(gbsw_sw64 *sw, int nsteps);
+
+/* As sw_volume: dx*dy*sum(H + eta) and the wet part, FP64 on the device in
+ * a fixed order; GBSW_ERR_NONFINITE if any eta is NaN or Inf.  Syncs. */
+gbsw_status sw64_volume(gbsw_sw64 *sw, double *volume, double *wet_volume);
+
+/* As sw_get_state with FP64 host buffers (any may be NULL): eta ny*nx,
+ * u ny*(nx+1), v (ny+1)*nx, wet ny*nx bytes.  Synchronous. */
+gbsw_status sw64_get_state(gbsw_sw64 *sw, double *eta, double *u, double *v, uint8_t *wet);
+
+/* Release the context.  NULL is ignored. */
+void sw64_destroy(gbsw_sw64 *sw);
+
+/* ------------------------------------------------------------------------
  * Batched 2DSW ensemble: n independent instances (each its own size,
  * bathymetry and initial state) of the 2DSW step above, advanced together.
  * The paper has no ensemble; this is the step of Sec. 6.2 applied to many

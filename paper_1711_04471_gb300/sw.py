@@ -77,6 +77,62 @@ class SW:
         self.close()
 
 
+class SW64:
+    """The 2DSW step in FP64 end to end (sw64_* entry points): the same
+    method and parameters as SW, three kernels per step, every operation
+    rounded as written."""
+
+    def __init__(self, params: dict, H: np.ndarray, eta0: np.ndarray, stream=None):
+        L = N.lib()
+        self.nx, self.ny = int(params["nx"]), int(params["ny"])
+        p = N.SWParams(self.nx, self.ny, params["dx"], params["dy"], params["dt"],
+                       params.get("g", 9.81), params.get("eps", 0.05), params.get("hmin", 0.05))
+        H = np.ascontiguousarray(H, dtype=np.float64)
+        eta0 = np.ascontiguousarray(eta0, dtype=np.float64)
+        if H.shape != (self.ny, self.nx) or eta0.shape != (self.ny, self.nx):
+            raise ValueError("H and eta0 must be (ny, nx)")
+        h = C.c_void_p()
+        N.check(L.sw64_create(C.byref(p), N.ptr(H, C.c_double), N.ptr(eta0, C.c_double),
+                              N.stream_handle(stream), C.byref(h)), "sw64_create")
+        self._h = h
+
+    def step(self, nsteps: int) -> "SW64":
+        N.check(N.lib().sw64_step(self._h, int(nsteps)), "sw64_step")
+        return self
+
+    def volume(self):
+        v, w = C.c_double(), C.c_double()
+        N.check(N.lib().sw64_volume(self._h, C.byref(v), C.byref(w)), "sw64_volume")
+        return v.value, w.value
+
+    def get_state(self):
+        nx, ny = self.nx, self.ny
+        eta = np.empty((ny, nx))
+        u = np.empty((ny, nx + 1))
+        v = np.empty((ny + 1, nx))
+        wet = np.empty((ny, nx), np.uint8)
+        N.check(N.lib().sw64_get_state(self._h, N.ptr(eta, C.c_double), N.ptr(u, C.c_double),
+                                       N.ptr(v, C.c_double), N.ptr(wet, C.c_uint8)), "sw64_get_state")
+        return dict(eta=eta, u=u, v=v, wet=wet)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            N.lib().sw64_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
 class SWBatch:
     """Ensemble of independent 2DSW instances stepped by one persistent
     kernel (sw_batch_* entry points)."""
