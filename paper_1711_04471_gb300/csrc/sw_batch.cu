@@ -95,7 +95,11 @@ sw_batch_kernel(BatchDev B, int nlevels, int cur0)
     __shared__ SWStageLines lines[T];
     __shared__ int s_item;
     for (int lv = 0; lv < nlevels; ++lv) {
-        const int a = (cur0 + lv) & 1, b = a ^ 1;
+        // buffer parity of this level, by selects (indexing the parameter's
+        // pointer arrays with a run-time index would copy them to local memory)
+        const bool odd = ((cur0 + lv) & 1) != 0;
+        const float *eta_a = odd ? B.eta[1] : B.eta[0], *u_a = odd ? B.u[1] : B.u[0], *v_a = odd ? B.v[1] : B.v[0];
+        float *eta_b = odd ? B.eta[0] : B.eta[1], *u_b = odd ? B.u[0] : B.u[1], *v_b = odd ? B.v[0] : B.v[1];
         for (;;) {
             if (threadIdx.x == 0) s_item = (int)atomicAdd(&B.counters[lv], 1u);
             __syncthreads();
@@ -104,8 +108,8 @@ sw_batch_kernel(BatchDev B, int nlevels, int cur0)
             if (it >= B.nitems) break;
             const SWItem w = B.items[it];
             const SWInst I = B.inst[w.inst];
-            sw_stream_tile<T, SWLoad::L2>(I.p, w.strip, w.r0, w.r1, B.H + I.off, B.eta[a] + I.off, B.u[a] + I.off,
-                                          B.v[a] + I.off, B.eta[b] + I.off, B.u[b] + I.off, B.v[b] + I.off, lines);
+            sw_stream_tile<T, SWLoad::L2>(I.p, w.strip, w.r0, w.r1, B.H + I.off, eta_a + I.off, u_a + I.off,
+                                          v_a + I.off, eta_b + I.off, u_b + I.off, v_b + I.off, lines);
         }
         if (lv + 1 < nlevels && !grid_barrier(B, gridDim.x)) return;
     }
