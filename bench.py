@@ -44,6 +44,15 @@ TRAFFIC_SW_STREAM_T3 = 458.705664e6
 WORKLOAD = "2DSW 4096x4096 wet/dry (15% dry), FP32, 100 time steps + FP64 volume per step"
 
 
+def _l2_mb():
+    """L2 size of the current device in MB (0 if unknown)."""
+    try:
+        import torch
+        return getattr(torch.cuda.get_device_properties(torch.cuda.current_device()), "L2_cache_size", 0) / 1e6
+    except Exception:
+        return 0.0
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -433,7 +442,8 @@ def run_les(args, rank, world, local, learned):
                                    "tol 1e-6 (FP64), warm start " + ("U-Net vs previous pressure" if learned
                                                                      else "previous pressure"),
                        "spinup_steps": args.spinup, "check_every": args.check_every,
-                       "l2": "e and r (71 MB) stay in L2 between sweeps; that reuse is the method's own"},
+                       "l2": f"e and r (71 MB) stay in the {_l2_mb():.0f} MB L2 between sweeps; that reuse is the "
+                             "method's own"},
             "clocks": clk,
             "sor_iters_per_step": iters,
             "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 #include <stdio.h>
 
@@ -54,6 +55,23 @@ inline size_t round_up(size_t a, size_t b) { return (a + b - 1) / b * b; }
 
 // Number of SMs of the current device (cached per process).
 int sm_count();
+
+// Host-side fault injection for tests, from the GBSW_FAULT environment
+// variable (read at each call): "alloc" makes the create calls return
+// GBSW_ERR_OOM before any device allocation; "sync_timeout" gives the
+// ensemble kernel's grid barrier a zero spin budget, so that its bounded
+// wait gives up and the call reports GBSW_ERR_TIMEOUT.  No injection
+// faults, traps or hangs a device.
+bool fault_injected(const char *what);
+
+// NVTX range over a host scope (shown by profilers that record NVTX; the
+// header-only NVTX library makes it a no-op otherwise).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // ---------------------------------------------------------------------------
 // Deterministic FP64 block reduction: every thread contributes one value;

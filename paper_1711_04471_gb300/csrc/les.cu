@@ -404,6 +404,7 @@ gbsw_status les_create(const gbsw_les_params *params, const uint8_t *solid, void
         !(P.omega > 0 && P.omega < 2) || !(P.tol >= 0) || P.max_iter < 0 || P.check_every < 1 || P.check_every > 1000)
         return GBSW_ERR_ARG;
     if (0.5 * P.dx <= P.z0) return GBSW_ERR_ARG;
+    if (fault_injected("alloc")) return GBSW_ERR_OOM;
     // advective CFL of the fastest inflow speed
     double umax = 0.0;
     for (int k = 1; k <= P.nz; ++k) umax = std::max(umax, fabs(inflow_profile(P, k)));
@@ -476,6 +477,7 @@ gbsw_status les_create(const gbsw_les_params *params, const uint8_t *solid, void
 
 gbsw_status les_step(gbsw_les *s, int nsteps, gbsw_les_stats *stats)
 {
+    gbsw::NvtxRange nvtx_range("les_step");
     if (!s || nsteps < 0) return GBSW_ERR_ARG;
     if (nsteps == 0) return GBSW_OK;
     gbsw_status st = ensure_ctl_log(s, nsteps);

@@ -1,5 +1,6 @@
 // Library-wide helpers: status strings, last-error text, device queries.
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include "common.cuh"
@@ -23,6 +24,12 @@ int sm_count()
             n = 1;
     }
     return n;
+}
+
+bool fault_injected(const char *what)
+{
+    const char *v = getenv("GBSW_FAULT");
+    return v && strcmp(v, what) == 0;
 }
 
 }  // namespace gbsw

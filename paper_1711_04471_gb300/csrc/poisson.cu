@@ -512,6 +512,7 @@ extern "C" gbsw_status poisson_solve(int nx, int ny, int nz, double dx, float *p
                                      double tol, int max_iter, int check_every, void *stream, int *iters,
                                      double *rel_res)
 {
+    gbsw::NvtxRange nvtx_range("poisson_solve");
     if (nx < 2 || ny < 2 || nz < 2 || (ny & 1) || nx > 8192 || ny > 8192 || nz > 8192 || !(dx > 0) || !p || !b)
         return GBSW_ERR_ARG;
     const bool fixed = tol < 0.0;  // paper mode: exactly max_iter iterations, no convergence test

@@ -170,6 +170,7 @@ gbsw_status sw_create(const gbsw_sw_params *params, const double *H, const doubl
     }
     const double courant = sqrt(P.g * hmax) * P.dt * sqrt(1.0 / (P.dx * P.dx) + 1.0 / (P.dy * P.dy));
     if (courant > 1.0) return GBSW_ERR_CFL;
+    if (fault_injected("alloc")) return GBSW_ERR_OOM;
 
     gbsw_sw *s = (gbsw_sw *)calloc(1, sizeof(gbsw_sw));
     if (!s) return GBSW_ERR_OOM;
@@ -237,6 +238,7 @@ gbsw_status sw_set_blocking(gbsw_sw *s, int steps_per_launch)
 
 gbsw_status sw_step(gbsw_sw *s, int nsteps)
 {
+    gbsw::NvtxRange nvtx_range("sw_step");
     if (!s || nsteps < 0) return GBSW_ERR_ARG;
     const int T = s->blocking > 0 ? s->blocking : auto_blocking(s);
     int left = nsteps;
@@ -254,6 +256,7 @@ gbsw_status sw_step(gbsw_sw *s, int nsteps)
 
 gbsw_status sw_volume(gbsw_sw *s, double *volume, double *wet_volume)
 {
+    gbsw::NvtxRange nvtx_range("sw_volume");
     if (!s) return GBSW_ERR_ARG;
     sw_volume_partial_kernel<<<SW_VOL_BLOCKS, SW_VOL_THREADS, 0, s->stream>>>(s->d, s->H, s->eta[s->cur],
                                                                              s->partials);

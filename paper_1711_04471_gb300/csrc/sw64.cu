@@ -260,6 +260,7 @@ gbsw_status sw64_create(const gbsw_sw_params *params, const double *H, const dou
     }
     const double courant = sqrt(P.g * hmax) * P.dt * sqrt(1.0 / (P.dx * P.dx) + 1.0 / (P.dy * P.dy));
     if (courant > 1.0) return GBSW_ERR_CFL;
+    if (fault_injected("alloc")) return GBSW_ERR_OOM;
 
     gbsw_sw64 *s = new (std::nothrow) gbsw_sw64();
     if (!s) return GBSW_ERR_OOM;
@@ -299,6 +300,7 @@ gbsw_status sw64_create(const gbsw_sw_params *params, const double *H, const dou
 
 gbsw_status sw64_step(gbsw_sw64 *s, int nsteps)
 {
+    gbsw::NvtxRange nvtx_range("sw64_step");
     if (!s || nsteps < 0) return GBSW_ERR_ARG;
     const S64Dev d = s64_dev(s);
     const dim3 gf(ceil_div(d.nx + 1, S64_THREADS), d.ny + 1), gc(ceil_div(d.nx, S64_THREADS), d.ny);

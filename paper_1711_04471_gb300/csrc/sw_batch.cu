@@ -50,6 +50,7 @@ struct BatchDev {
     unsigned *counters;  // one work counter per level
     unsigned *bar_count, *bar_gen;
     int *status;
+    long long spin_limit;  // polls of a grid-barrier wait before it gives up
 };
 
 constexpr long long SPIN_LIMIT = 20000000;  // ~ seconds; a level takes milliseconds
@@ -72,7 +73,7 @@ __device__ bool grid_barrier(const BatchDev &B, unsigned nblocks)
         } else {
             long long spins = 0;
             while (atomicAdd(B.bar_gen, 0u) == g) {
-                if (++spins > SPIN_LIMIT) {
+                if (++spins > B.spin_limit) {
                     atomicCAS(B.status, DEV_OK, DEV_TIMEOUT);
                     break;
                 }
@@ -241,6 +242,7 @@ gbsw_status launch_batch(gbsw_sw_batch *b, cudaStream_t s, int nlevels, int cur0
     B.bar_count = b->bar;
     B.bar_gen = b->bar + 1;
     B.status = b->status;
+    B.spin_limit = fault_injected("sync_timeout") ? 0 : SPIN_LIMIT;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(SWS_THREADS);
@@ -299,6 +301,7 @@ gbsw_status sw_batch_create(int n, const gbsw_sw_params *params, const double *c
                             void *stream, gbsw_sw_batch **out)
 {
     if (n < 1 || !params || !H || !eta0 || !out) return GBSW_ERR_ARG;
+    if (fault_injected("alloc")) return GBSW_ERR_OOM;
     gbsw_sw_batch *b = new (std::nothrow) gbsw_sw_batch();
     if (!b) return GBSW_ERR_OOM;
     b->n = n;
@@ -407,6 +410,7 @@ gbsw_status sw_batch_get_tiling(gbsw_sw_batch *b, int *steps_per_level, int *row
 
 gbsw_status sw_batch_step(gbsw_sw_batch *b, int nsteps)
 {
+    gbsw::NvtxRange nvtx_range("sw_batch_step");
     if (!b || nsteps < 0) return GBSW_ERR_ARG;
     if (nsteps == 0) return GBSW_OK;
     const int full = nsteps / b->T, tail = nsteps % b->T;
@@ -493,6 +497,7 @@ gbsw_status sw_batch_step_separate(gbsw_sw_batch *b, int nsteps)
 
 gbsw_status sw_batch_volumes(gbsw_sw_batch *b, double *volumes, double *wet_volumes)
 {
+    gbsw::NvtxRange nvtx_range("sw_batch_volumes");
     if (!b) return GBSW_ERR_ARG;
     sw_batch_volume_partial<<<dim3(VOL_BLOCKS, b->n), SW_VOL_THREADS, 0, b->stream>>>(b->inst, b->H, b->eta[b->cur],
                                                                                   b->partials);
@@ -539,6 +544,7 @@ gbsw_status sw_batch_get_state(gbsw_sw_batch *b, int m, float *eta, float *u, fl
  * restored), keep the fastest.  cache_path may be NULL. */
 gbsw_status sw_batch_autotune(gbsw_sw_batch *b, int trial_steps, const char *cache_path, int *T_out, int *rows_out)
 {
+    gbsw::NvtxRange nvtx_range("sw_batch_autotune");
     if (!b || trial_steps < 1) return GBSW_ERR_ARG;
     // cache key: device, instance count and sizes
     cudaDeviceProp prop;

@@ -342,6 +342,7 @@ int unet_num_params(void) { return param_count(); }
 gbsw_status unet_create(unsigned long long seed, void *stream, gbsw_unet **out)
 {
     if (!out) return GBSW_ERR_ARG;
+    if (fault_injected("alloc")) return GBSW_ERR_OOM;
     gbsw_unet *u = new (std::nothrow) gbsw_unet();
     if (!u) return GBSW_ERR_OOM;
     u->stream = (cudaStream_t)stream;
@@ -419,6 +420,7 @@ static gbsw_status check_status(gbsw_unet *u)
 
 gbsw_status unet_forward(gbsw_unet *u, int n, int D, int H, int W, const float *x, float *y)
 {
+    gbsw::NvtxRange nvtx_range("unet_forward");
     if (!u || !x || !y) return GBSW_ERR_ARG;
     Acts *a = nullptr;
     TRY(get_acts(u, n, D, H, W, false, &a));
@@ -432,6 +434,7 @@ gbsw_status unet_forward(gbsw_unet *u, int n, int D, int H, int W, const float *
 gbsw_status unet_gradients(gbsw_unet *u, int n, int D, int H, int W, const float *x, const float *target,
                            float *grads_host, double *loss)
 {
+    gbsw::NvtxRange nvtx_range("unet_gradients");
     if (!u || !x || !target) return GBSW_ERR_ARG;
     Acts *a = nullptr;
     TRY(get_acts(u, n, D, H, W, true, &a));
@@ -452,6 +455,7 @@ gbsw_status unet_gradients(gbsw_unet *u, int n, int D, int H, int W, const float
 gbsw_status unet_train_step(gbsw_unet *u, int n, int D, int H, int W, const float *x, const float *target, float lr,
                             double *loss)
 {
+    gbsw::NvtxRange nvtx_range("unet_train_step");
     if (!u || !x || !target || !(lr > 0)) return GBSW_ERR_ARG;
     Acts *a = nullptr;
     TRY(get_acts(u, n, D, H, W, true, &a));

@@ -66,3 +66,27 @@ def test_sor_division_selftest_rejects_bad_arguments(lib):
     assert lib.gbsw_selftest_sor_division(3, counts) == -1
     assert lib.gbsw_selftest_sor_division(8, counts) == -1
     assert lib.gbsw_selftest_sor_division(6, None) == -1
+
+
+def test_ensemble_barrier_timeout_is_reported(lib, monkeypatch):
+    """GBSW_FAULT=sync_timeout gives the persistent ensemble kernel's grid
+    barrier a zero spin budget: the first wait gives up, every block leaves,
+    and the next syncing call reports GBSW_ERR_TIMEOUT.  A new ensemble
+    without the injection then runs normally on the same context."""
+    from paper_1711_04471_gb300.sw import SWBatch
+    from paper_1711_04471_gb300._native import GBSWError
+    members = [inputs.sw_ensemble_member(n, 1002, k) for k, n in enumerate((64, 96, 130, 200))]
+    monkeypatch.setenv("GBSW_FAULT", "sync_timeout")
+    b = SWBatch(members)
+    b.set_tiling(2, 64)
+    b.step(6)                      # three levels: two grid barriers
+    with pytest.raises(GBSWError) as e:
+        b.volumes()
+    assert e.value.status == -6
+    b.close()
+    monkeypatch.delenv("GBSW_FAULT")
+    with SWBatch(members) as ok:
+        ok.set_tiling(2, 64)
+        ok.step(6)
+        vols, _ = ok.volumes()
+    assert np.all(np.isfinite(vols))
