@@ -401,7 +401,7 @@ def run_les(args, rank, world, local, learned):
     P.build()
     torch.cuda.set_device(local)
     shape = (256, 256, 128)
-    solid = inputs.les_buildings(*shape, dx=4.0, seed=1003)
+    solid = inputs.les_buildings(*shape, dx=4.0, seed=args.les_seed)
     kw = dict(check_every=args.check_every, max_iter=400000)
     rows = []
     clocks = ClockSampler(torch.cuda.current_device())
@@ -411,8 +411,8 @@ def run_les(args, rank, world, local, learned):
         from paper_1711_04471_gb300.unet import UNet
         net = UNet(seed=0)
         net.set_params(np.load(args.weights))
-        rows = train_unet.compare_warm_starts(net, shape=shape, spinup=args.spinup, steps=args.steps,
-                                              log=lambda *a: None, **kw)
+        rows = train_unet.compare_warm_starts(net, shape=shape, seed=args.les_seed, spinup=args.spinup,
+                                              steps=args.steps, log=lambda *a: None, **kw)
         net.close()
         t_plain = sum(r["plain_ms"] for r in rows) / len(rows)
         t_nn = sum(r["nn_ms"] for r in rows) / len(rows)
@@ -438,7 +438,8 @@ def run_les(args, rank, world, local, learned):
             "warmup": args.spinup, "ms_per_step": t_nn if learned else t_plain, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 sweeps, f64 pressure and norms",
             "data": "synthetic",
-            "config": {"workload": "UFLES 256x256x128, dx 4 m, dt 0.025 s, 20 % building cover, SOR omega 1.8, "
+            "config": {"workload": f"UFLES 256x256x128, dx 4 m, dt 0.025 s, 20 % building cover (building seed "
+                                   f"{args.les_seed}), SOR omega 1.8, "
                                    "tol 1e-6 (FP64), warm start " + ("U-Net vs previous pressure" if learned
                                                                      else "previous pressure"),
                        "spinup_steps": args.spinup, "check_every": args.check_every,
@@ -590,6 +591,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--check-every", type=int, default=500,
                     help="les workloads: SOR iterations between FP64 residual checks")
+    ap.add_argument("--les-seed", type=int, default=1003,
+                    help="les workloads: building layout seed (1003: the benchmark layout)")
     ap.add_argument("--members", type=int, default=512,
                     help="ensemble workload: the first N of the 512 instances (smaller cases for profiling)")
     args = ap.parse_args()
