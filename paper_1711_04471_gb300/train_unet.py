@@ -21,7 +21,13 @@ coarse tensors by augment), and any linear combination of pairs is a pair
 Everything runs through the C ABI (les_*, warm_start_*, unet_*); the samples
 stay in device memory.
 
-    python -m paper_1711_04471_gb300.train_unet --out weights.npy
+The committed weights come from 13 runs (5 with base seed 3000, 8 with base
+seed 2000; the last one held out), generated and saved separately and then
+trained on together:
+
+    python -m paper_1711_04471_gb300.train_unet --seeds 5 --base-seed 3000 --iters 0 --out x.npy --save-data b.npz
+    python -m paper_1711_04471_gb300.train_unet --seeds 8 --base-seed 2000 --iters 0 --out x.npy --save-data a.npz
+    python -m paper_1711_04471_gb300.train_unet --data b.npz a.npz --out weights.npy
 """
 from __future__ import annotations
 
@@ -226,7 +232,10 @@ def main():
     ap.add_argument("--steps", type=int, default=32, help="solved steps per run")
     ap.add_argument("--start", type=int, default=17, help="steps before the first pair")
     ap.add_argument("--factor", type=int, default=16)
-    ap.add_argument("--data", help="load the solved pairs from this .npz instead of running the LES")
+    ap.add_argument("--data", nargs="+", help="load the solved pairs from these .npz files (in order; the last "
+                                               "run of the last file is held out) instead of running the LES")
+    ap.add_argument("--base-seed", type=int, default=2000, help="building seeds of the generated runs: "
+                                                                 "derive_seed(base, k)")
     ap.add_argument("--save-data", help="write the solved pairs to this .npz")
     ap.add_argument("--iters", type=int, default=60000)
     ap.add_argument("--batch", type=int, default=32)
@@ -240,10 +249,12 @@ def main():
     build()
     from .unet import UNet
     if args.data:
-        z = np.load(args.data)
-        data = [tuple(torch.from_numpy(z[f"{a}{k}"]).cuda() for a in "xts") for k in range(int(z["nseeds"]))]
+        data = []
+        for path in args.data:
+            z = np.load(path)
+            data += [tuple(torch.from_numpy(z[f"{a}{k}"]).cuda() for a in "xts") for k in range(int(z["nseeds"]))]
     else:
-        data = generate(args.seeds, args.steps, start=args.start, f=args.factor)
+        data = generate(args.seeds, args.steps, start=args.start, f=args.factor, base_seed=args.base_seed)
     if args.save_data:
         arrs = {"nseeds": np.array(len(data))}
         for k, (x, t, s) in enumerate(data):
