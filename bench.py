@@ -42,6 +42,11 @@ METRIC = "cell-updates/s"
 # set to None whenever that kernel changes until it is captured again.
 TRAFFIC_SW_STREAM_T3 = 458.705664e6
 WORKLOAD = "2DSW 4096x4096 wet/dry (15% dry), FP32, 100 time steps + FP64 volume per step"
+# DRAM bytes (read + write) of one SOR iteration (red + black half-sweep) on
+# the 256x256x128 grid with the L2 warm, from the ncu capture summarised in
+# profiles/sor_sweep_kernel_256x256x128.md; None whenever that kernel changes
+# until it is captured again.
+TRAFFIC_SOR_ITER_256 = (1.734144 + 0.464896 + 2.585344 + 0.501504) * 1e6
 
 
 def _l2_mb():
@@ -448,7 +453,9 @@ def run_les(args, rank, world, local, learned):
             "clocks": clk,
             "sor_iters_per_step": iters,
             "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                         "traffic": None, "peak_kind": peak_kind, "kernel": "sor_sweep_kernel",
+                         "traffic": TRAFFIC_SOR_ITER_256 if shape == (256, 256, 128) else None,
+                         "traffic_unit": "bytes per SOR iteration (two half-sweeps), warm L2",
+                         "peak_kind": peak_kind, "kernel": "sor_sweep_kernel",
                          "per_unit": "12 B/cell/iteration x 8388608 cells (solve time / iterations)"},
             "cpu_baseline": None if t_pred is None else {
                 "value": (t_pred + iters * t_iter) * 1e3, "unit": "ms/step", "cores": 1, "kind": "oracle",
