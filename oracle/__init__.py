@@ -13,15 +13,33 @@ import numpy as np
 
 from . import build as _build
 
-_lib = None
+_libs = {}
+_use_openmp = False
 
 
-def lib():
-    global _lib
-    if _lib is None:
-        _lib = C.CDLL(_build.build())
-        _declare(_lib)
-    return _lib
+def lib(openmp: bool | None = None):
+    """The serial oracle library, or its OpenMP build (same sources, outer
+    loops of the maps on all host cores, bitwise equal results).  With
+    openmp=None, the build chosen by use_openmp()."""
+    key = _use_openmp if openmp is None else bool(openmp)
+    if key not in _libs:
+        L = C.CDLL(_build.build(openmp=key))
+        _declare(L)
+        _libs[key] = L
+    return _libs[key]
+
+
+def use_openmp(flag: bool) -> None:
+    """Route every oracle call that does not name a build to the OpenMP
+    build (True) or the serial one (False, the default)."""
+    global _use_openmp
+    _use_openmp = bool(flag)
+
+
+def threads(n: int = 0, openmp: bool = True) -> int:
+    """Threads of the OpenMP build's parallel maps (n > 0 sets it); 1 for
+    the serial build."""
+    return int(lib(openmp).oracle_threads(int(n)))
 
 
 class SWParams(C.Structure):
@@ -38,6 +56,8 @@ def _declare(L):
     L.oracle_sw_run.restype = C.c_int
     L.oracle_sw_volume.argtypes = [C.POINTER(SWParams), _dp, _dp, C.POINTER(C.c_double), C.POINTER(C.c_double)]
     L.oracle_sw_volume.restype = None
+    L.oracle_threads.argtypes = [C.c_int]
+    L.oracle_threads.restype = C.c_int
     if hasattr(L, "oracle_les_declare_marker"):
         from . import les as _les
         _les.declare(L)

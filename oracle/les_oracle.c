@@ -39,10 +39,20 @@
  *
  * Arrays are (nz+2)*(ny+2)*(nx+2) doubles, x fastest.
  * Build with -O2 -ffp-contract=off.
+ *
+ * Threads: built with -fopenmp (the all-cores timing build), the outer loop
+ * of each per-cell map runs in parallel, and the two colours of an SOR
+ * iteration stay in order (cells of one colour read only the other
+ * colour).  The residual norms are summed serially in the same cell order
+ * in both builds (the OpenMP build first stores the per-cell terms), so
+ * both builds give bitwise equal results.
  */
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 typedef struct {
     int nx, ny, nz;
@@ -71,6 +81,7 @@ void oracle_les_velnw(const oracle_les_params *P, const double *p, double *u, do
 {
     const int nx = P->nx, ny = P->ny, nz = P->nz;
     const double c = P->dt / P->dx;
+#pragma omp parallel for schedule(static)
     for (int k = 1; k <= nz; ++k)
         for (int j = 1; j <= ny; ++j)
             for (int i = 1; i <= nx; ++i) {
@@ -87,6 +98,7 @@ void oracle_les_velnw(const oracle_les_params *P, const double *p, double *u, do
 void oracle_les_bondv1(const oracle_les_params *P, double *u, double *v, double *w)
 {
     const int nx = P->nx, ny = P->ny, nz = P->nz;
+#pragma omp parallel for schedule(static)
     for (int k = 1; k <= nz; ++k)
         for (int j = 1; j <= ny; ++j) {
             u[ID(0, j, k)] = inflow_u(P, k);
@@ -96,6 +108,7 @@ void oracle_les_bondv1(const oracle_les_params *P, double *u, double *v, double 
             w[ID(0, j, k)] = -w[ID(1, j, k)];
             w[ID(nx + 1, j, k)] = w[ID(nx, j, k)];
         }
+#pragma omp parallel for schedule(static)
     for (int k = 1; k <= nz; ++k)
         for (int i = 0; i <= nx + 1; ++i) {
             u[ID(i, 0, k)] = u[ID(i, ny, k)];
@@ -105,6 +118,7 @@ void oracle_les_bondv1(const oracle_les_params *P, double *u, double *v, double 
             w[ID(i, 0, k)] = w[ID(i, ny, k)];
             w[ID(i, ny + 1, k)] = w[ID(i, 1, k)];
         }
+#pragma omp parallel for schedule(static)
     for (int j = 0; j <= ny + 1; ++j)
         for (int i = 0; i <= nx + 1; ++i) {
             u[ID(i, j, 0)] = -u[ID(i, j, 1)];
@@ -129,6 +143,7 @@ void oracle_les_velfg(const oracle_les_params *P, const double *u, const double 
     memset(fv, 0, n * sizeof(double));
     memset(fw, 0, n * sizeof(double));
     const double r = 1.0 / P->dx;
+#pragma omp parallel for schedule(static)
     for (int k = 1; k <= nz; ++k)
         for (int j = 1; j <= ny; ++j)
             for (int i = 1; i <= nx; ++i) {
@@ -173,6 +188,7 @@ void oracle_les_feedbf(const oracle_les_params *P, const unsigned char *solid, c
     const int nx = P->nx, ny = P->ny, nz = P->nz;
     /* solid is nz*ny*nx without ghosts */
 #define SOL(i, j, k) (solid[((size_t)((k) - 1) * ny + (size_t)((j) - 1)) * nx + (size_t)((i) - 1)])
+#pragma omp parallel for schedule(static)
     for (int k = 1; k <= nz; ++k)
         for (int j = 1; j <= ny; ++j)
             for (int i = 1; i <= nx; ++i) {
@@ -218,6 +234,7 @@ void oracle_les_nut(const oracle_les_params *P, const double *u, const double *v
 {
     const int nx = P->nx, ny = P->ny, nz = P->nz;
     const double l2 = (P->cs * P->dx) * (P->cs * P->dx);
+#pragma omp parallel for schedule(static)
     for (int k = 1; k <= nz; ++k)
         for (int j = 1; j <= ny; ++j)
             for (int i = 1; i <= nx; ++i) {
@@ -276,6 +293,7 @@ void oracle_les_visc(const oracle_les_params *P, const double *u, const double *
 #define T12(i, j, k) (2.0 * NU_XY(i, j, k) * s12_edge(P, u, v, i, j, k))
 #define T13(i, j, k) (2.0 * NU_XZ(i, j, k) * s13_edge(P, u, w, i, j, k))
 #define T23(i, j, k) (2.0 * NU_YZ(i, j, k) * s23_edge(P, v, w, i, j, k))
+#pragma omp parallel for schedule(static)
     for (int k = 1; k <= nz; ++k)
         for (int j = 1; j <= ny; ++j)
             for (int i = 1; i <= nx; ++i) {
@@ -306,6 +324,7 @@ void oracle_les_adam(const oracle_les_params *P, int first, double *u, double *v
 {
     const int nx = P->nx, ny = P->ny, nz = P->nz;
     const double dt = P->dt;
+#pragma omp parallel for schedule(static)
     for (int k = 1; k <= nz; ++k)
         for (int j = 1; j <= ny; ++j)
             for (int i = 1; i <= nx; ++i) {
@@ -331,6 +350,7 @@ void oracle_les_rhs(const oracle_les_params *P, const double *u, const double *v
 {
     const int nx = P->nx, ny = P->ny, nz = P->nz;
     const double c = 1.0 / (P->dx * P->dt);
+#pragma omp parallel for schedule(static)
     for (int k = 1; k <= nz; ++k)
         for (int j = 1; j <= ny; ++j)
             for (int i = 1; i <= nx; ++i) {
@@ -359,6 +379,7 @@ static void les_stencil(const oracle_les_params *P, const double *p, int i, int 
 void oracle_les_apply_A(const oracle_les_params *P, const double *p, double *Ap)
 {
     const double r2 = 1.0 / (P->dx * P->dx);
+#pragma omp parallel for schedule(static)
     for (int k = 1; k <= P->nz; ++k)
         for (int j = 1; j <= P->ny; ++j)
             for (int i = 1; i <= P->nx; ++i) {
@@ -368,21 +389,68 @@ void oracle_les_apply_A(const oracle_les_params *P, const double *p, double *Ap)
             }
 }
 
-/* ||b - A p||_2 / ||b||_2 over interior cells (0 if ||b|| == 0). */
-double oracle_les_residual(const oracle_les_params *P, const double *b, const double *p)
+/* Residual of cell (i,j,k): b - A p. */
+static double les_res_cell(const oracle_les_params *P, const double *b, const double *p, double r2, int i, int j,
+                           int k)
+{
+    double s, d;
+    les_stencil(P, p, i, j, k, &s, &d);
+    return b[ID(i, j, k)] - (s - d * p[ID(i, j, k)]) * r2;
+}
+
+/* ||b - A p||_2 / ||b||_2 over interior cells (0 if ||b|| == 0); the sums
+ * run over the cells in (k, j, i) order.  work: NULL, or (OpenMP build)
+ * 2 nx ny nz doubles for the per-cell terms, formed in parallel. */
+static double les_residual_w(const oracle_les_params *P, const double *b, const double *p, double *work)
 {
     const double r2 = 1.0 / (P->dx * P->dx);
+    const int nx = P->nx, ny = P->ny, nz = P->nz;
     double rr = 0.0, bb = 0.0;
-    for (int k = 1; k <= P->nz; ++k)
-        for (int j = 1; j <= P->ny; ++j)
-            for (int i = 1; i <= P->nx; ++i) {
-                double s, d;
-                les_stencil(P, p, i, j, k, &s, &d);
-                double res = b[ID(i, j, k)] - (s - d * p[ID(i, j, k)]) * r2;
-                rr += res * res;
-                bb += b[ID(i, j, k)] * b[ID(i, j, k)];
-            }
+    if (work) {
+        const size_t nc = (size_t)nx * ny * nz;
+#pragma omp parallel for schedule(static)
+        for (int k = 1; k <= nz; ++k)
+            for (int j = 1; j <= ny; ++j)
+                for (int i = 1; i <= nx; ++i) {
+                    const size_t q = ((size_t)(k - 1) * ny + (j - 1)) * nx + (i - 1);
+                    const double res = les_res_cell(P, b, p, r2, i, j, k);
+                    work[q] = res * res;
+                    work[nc + q] = b[ID(i, j, k)] * b[ID(i, j, k)];
+                }
+        for (size_t q = 0; q < nc; ++q) {
+            rr += work[q];
+            bb += work[nc + q];
+        }
+    } else {
+        for (int k = 1; k <= nz; ++k)
+            for (int j = 1; j <= ny; ++j)
+                for (int i = 1; i <= nx; ++i) {
+                    const double res = les_res_cell(P, b, p, r2, i, j, k);
+                    rr += res * res;
+                    bb += b[ID(i, j, k)] * b[ID(i, j, k)];
+                }
+    }
     return bb > 0.0 ? sqrt(rr / bb) : 0.0;
+}
+
+/* Scratch for the per-cell residual terms in the OpenMP build (NULL in the
+ * serial build, or if the allocation fails: the serial sum is then used). */
+static double *les_residual_work(const oracle_les_params *P)
+{
+#ifdef _OPENMP
+    return (double *)malloc(2 * (size_t)P->nx * P->ny * P->nz * sizeof(double));
+#else
+    (void)P;
+    return NULL;
+#endif
+}
+
+double oracle_les_residual(const oracle_les_params *P, const double *b, const double *p)
+{
+    double *work = les_residual_work(P);
+    const double rho = les_residual_w(P, b, p, work);
+    free(work);
+    return rho;
 }
 
 /* One red-black SOR iteration: cells with (i+j+k) even first, then odd. */
@@ -390,6 +458,7 @@ static void les_sor_sweep(const oracle_les_params *P, const double *b, double *p
 {
     const double h2 = P->dx * P->dx;
     for (int colour = 0; colour < 2; ++colour)
+#pragma omp parallel for schedule(static)
         for (int k = 1; k <= P->nz; ++k)
             for (int j = 1; j <= P->ny; ++j)
                 for (int i = 1; i <= P->nx; ++i) {
@@ -406,13 +475,15 @@ static void les_sor_sweep(const oracle_les_params *P, const double *b, double *p
 int oracle_les_sor(const oracle_les_params *P, const double *b, double *p, double omega, double tol,
                    int max_iter, int *iters, double *rel_res)
 {
-    double rho = oracle_les_residual(P, b, p);
+    double *work = les_residual_work(P);
+    double rho = les_residual_w(P, b, p, work);
     int it = 0;
     while (rho > tol && it < max_iter) {
         les_sor_sweep(P, b, p, omega);
         ++it;
-        rho = oracle_les_residual(P, b, p);
+        rho = les_residual_w(P, b, p, work);
     }
+    free(work);
     *iters = it;
     *rel_res = rho;
     return rho <= tol ? 0 : 1;

@@ -31,10 +31,18 @@
  * Arrays are (ny+2) x (nx+2) doubles, row-major, x fastest, index
  * j*(nx+2) + i.  Build with -O2 -ffp-contract=off so every operation rounds
  * as written.
+ *
+ * Threads: built with -fopenmp (the all-cores timing build), the outer loop
+ * of each per-cell map runs in parallel.  Every cell's value is computed by
+ * the same expression either way, and the volume sum stays serial, so both
+ * builds give bitwise equal results.
  */
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define IDX(i, j) ((size_t)(j) * (size_t)(nx + 2) + (size_t)(i))
 
@@ -48,6 +56,7 @@ static void sw_depth_and_mask(const oracle_sw_params *p, const double *H, const 
                               double *h, unsigned char *wet)
 {
     const int nx = p->nx, ny = p->ny;
+#pragma omp parallel for schedule(static)
     for (int j = 0; j <= ny + 1; ++j)
         for (int i = 0; i <= nx + 1; ++i) {
             int interior = (i >= 1 && i <= nx && j >= 1 && j <= ny);
@@ -72,6 +81,7 @@ static void sw_dyn_momentum(const oracle_sw_params *p, const double *eta, const 
                             const double *u, const double *v, double *un, double *vn)
 {
     const int nx = p->nx, ny = p->ny;
+#pragma omp parallel for schedule(static)
     for (int j = 1; j <= ny; ++j)
         for (int i = 0; i <= nx; ++i) {
             double val = 0.0;
@@ -81,6 +91,7 @@ static void sw_dyn_momentum(const oracle_sw_params *p, const double *eta, const 
             }
             un[IDX(i, j)] = val;
         }
+#pragma omp parallel for schedule(static)
     for (int j = 0; j <= ny; ++j)
         for (int i = 1; i <= nx; ++i) {
             double val = 0.0;
@@ -105,6 +116,7 @@ static void sw_dyn_continuity(const oracle_sw_params *p, const double *h, const 
                               const double *vn, const double *eta, double *eta_star)
 {
     const int nx = p->nx, ny = p->ny;
+#pragma omp parallel for schedule(static)
     for (int j = 1; j <= ny; ++j)
         for (int i = 1; i <= nx; ++i) {
             double fe = sw_upwind_flux(un[IDX(i, j)], h[IDX(i, j)], h[IDX(i + 1, j)]);
@@ -121,6 +133,7 @@ static void sw_shapiro(const oracle_sw_params *p, const unsigned char *wet, cons
 {
     const int nx = p->nx, ny = p->ny;
     const double q = 0.25 * p->eps;
+#pragma omp parallel for schedule(static)
     for (int j = 1; j <= ny; ++j)
         for (int i = 1; i <= nx; ++i) {
             if (!wet[IDX(i, j)]) {
@@ -181,6 +194,7 @@ int oracle_sw_run(const oracle_sw_params *p, const double *H, double *eta, doubl
     double m = INFINITY;
     for (int s = 0; s < nsteps; ++s) {
         sw_depth_and_mask(p, H, eta, w.h, w.wet);
+#pragma omp parallel for schedule(static) reduction(min : m)
         for (int j = 1; j <= ny; ++j)
             for (int i = 1; i <= nx; ++i) {
                 double d = fabs(w.h[IDX(i, j)] - p->hmin);
@@ -190,6 +204,7 @@ int oracle_sw_run(const oracle_sw_params *p, const double *H, double *eta, doubl
         sw_dyn_continuity(p, w.h, w.un, w.vn, eta, w.eta_star);
         sw_shapiro(p, w.wet, w.eta_star, w.eta_new);
         /* Step 5: state update. */
+#pragma omp parallel for schedule(static)
         for (int j = 1; j <= ny; ++j)
             for (int i = 1; i <= nx; ++i)
                 eta[IDX(i, j)] = w.eta_new[IDX(i, j)];
@@ -198,6 +213,7 @@ int oracle_sw_run(const oracle_sw_params *p, const double *H, double *eta, doubl
     }
     /* The margin also covers the final state, which decides the last mask. */
     sw_depth_and_mask(p, H, eta, w.h, w.wet);
+#pragma omp parallel for schedule(static) reduction(min : m)
     for (int j = 1; j <= ny; ++j)
         for (int i = 1; i <= nx; ++i) {
             double d = fabs(w.h[IDX(i, j)] - p->hmin);
@@ -225,4 +241,16 @@ void oracle_sw_volume(const oracle_sw_params *p, const double *H, const double *
         }
     *volume = s * p->dx * p->dy;
     *wet_volume = sw * p->dx * p->dy;
+}
+
+/* Threads the parallel maps use (1 in the serial build); n > 0 sets it. */
+int oracle_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }
