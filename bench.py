@@ -6,11 +6,17 @@ instances, persistent kernel vs separate launches), ``les`` (256x256x128
 UFLES step at 1e-6 residual) and ``les-nn`` (the same, learned warm start
 vs previous-pressure warm start on the same states).
 
-One benchmark step = 100 model time steps of the 4096^2 grid (the fused
-momentum / continuity / Shapiro / update kernel, temporally blocked) plus
-the FP64 volume reduction, i.e. every 2DSW row of the hot path.  The state
-(268 MB of eta, u, v, H) is larger than the 129 MB L2, so no L2 flush is
-needed between steps.
+One benchmark step = 900 model time steps of the 4096^2 grid (the fused
+momentum / continuity / Shapiro / update kernel, temporally blocked: 300
+launches of 3 fused steps) plus the FP64 volume reduction, i.e. every 2DSW
+row of the hot path.  The state (268 MB of eta, u, v, H) is larger than the
+129 MB L2, so no L2 flush is needed between steps.
+
+The same line carries an ``les`` object: the UFLES 256x256x128 step at a
+1e-6 FP64 residual after 20 spin-up steps, the previous-pressure warm start
+and the learned (U-Net) warm start compared on the same 10 states, with
+device times, SOR iterations, end-to-end wall time through les_step and the
+FP64 oracle on the host cores.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gbsw|reference]
 
@@ -21,6 +27,7 @@ is bracketed by barriers and the slowest rank's time is reported.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -34,19 +41,70 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 N_CELLS_SIDE = 4096
-STEPS_PER_BENCH_STEP = 100
+STEPS_PER_BENCH_STEP = 900  # a multiple of every fusion depth 1..6: each launch fuses T whole steps
 BYTES_PER_CELL_UPDATE = 28  # read eta, u, v, H; write eta, u, v (FP32)
 METRIC = "cell-updates/s"
-# DRAM bytes (read + write) of one sw_stream_kernel<3> launch on the 4096^2
-# grid, from the ncu capture summarised in profiles/sw_stream_kernel_4096.md;
-# set to None whenever that kernel changes until it is captured again.
-TRAFFIC_SW_STREAM_T3 = 458.705664e6
-WORKLOAD = "2DSW 4096x4096 wet/dry (15% dry), FP32, 100 time steps + FP64 volume per step"
-# DRAM bytes (read + write) of one SOR iteration (red + black half-sweep) on
-# the 256x256x128 grid with the L2 warm, from the ncu capture summarised in
-# profiles/sor_sweep_kernel_256x256x128.md; None whenever that kernel changes
-# until it is captured again.
-TRAFFIC_SOR_ITER_256 = (1.734144 + 0.464896 + 2.585344 + 0.501504) * 1e6
+WORKLOAD = "2DSW 4096x4096 wet/dry (15% dry), FP32, 900 time steps + FP64 volume per step"
+CSRC = os.path.join(ROOT, "paper_1711_04471_gb300", "csrc")
+
+# DRAM bytes (read + write) per unit from ncu captures of the kernels below,
+# with the SHA-256 (first 16 hex digits) of the kernel's source files at the
+# time of the capture.  When a source changes the figure is stale: the
+# bench then reports traffic as null until the kernel is captured again.
+NCU_TRAFFIC = {
+    # one sw_stream_kernel<3> launch on the 4096^2 grid
+    "sw_stream_kernel<3>": (458.705664e6, ("sw_stream.cuh", "sw_kernels.cuh"), "a2f5ba752ad5f879"),
+    # one SOR iteration (red + black half-sweep) on 256x256x128, L2 warm
+    "sor_iteration_256x256x128": ((1.734144 + 0.464896 + 2.585344 + 0.501504) * 1e6, ("poisson.cu", "poisson.cuh"),
+                                  "52501699356f9faa"),
+}
+
+
+def source_hash(files) -> str:
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(key):
+    """(bytes per unit, None) if the capture matches today's source, else (None, why)."""
+    val, files, digest = NCU_TRAFFIC[key]
+    try:
+        now = source_hash(files)
+    except OSError:
+        return None, "kernel source not found"
+    if now != digest:
+        return None, f"stale: {'/'.join(files)} changed since the ncu capture"
+    return val, None
+
+
+def host_info() -> dict:
+    """Host cores and CPU model (the oracle's timing platform)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for ln in f:
+                    if ln.lower().startswith(("model name", "cpu part")):
+                        model = ln.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    try:
+        usable = len(os.sched_getaffinity(0))
+    except Exception:
+        usable = os.cpu_count()
+    return {"nproc": os.cpu_count(), "usable_cores": usable, "cpu_model": model or "unknown"}
 
 
 def _l2_mb():
@@ -150,17 +208,34 @@ def max_over_ranks(x, world):
     return float(t.item())
 
 
-def cpu_oracle_rate(nsteps=10, side=N_CELLS_SIDE):
-    """Time the FP64 oracle (single thread) on a bounded sample: nsteps time
-    steps of the full 4096^2 grid (the same synthetic input)."""
+def cpu_oracle_sw(nsteps_serial=20, nsteps_omp=60, side=N_CELLS_SIDE):
+    """The FP64 oracle on a bounded sample of the same workload (time steps
+    of the full 4096^2 grid): its serial build on one thread and its OpenMP
+    build on all host cores.  Returns the cpu_baseline object."""
     import oracle
     from paper_1711_04471_gb300 import inputs
     inp = inputs.sw_wetdry(n=side, seed=1001)
-    s = oracle.SWState(inp.params(), inp.H, inp.eta0)
-    t0 = time.perf_counter()
-    s.run(nsteps)
-    dt = time.perf_counter() - t0
-    return side * side * nsteps / dt, dt
+    res = {}
+    for omp, n in ((False, nsteps_serial), (True, nsteps_omp)):
+        oracle.use_openmp(omp)
+        try:
+            s = oracle.SWState(inp.params(), inp.H, inp.eta0)
+            s.run(1)
+            t0 = time.perf_counter()
+            s.run(n)
+            dt = time.perf_counter() - t0
+        finally:
+            oracle.use_openmp(False)
+        res[omp] = (side * side * n / dt, dt, n)
+    threads = oracle.threads()
+    v, dt, n = res[True]
+    v1, dt1, n1 = res[False]
+    return {"value": v, "unit": METRIC, "cores": threads, "kind": "oracle",
+            "sample": f"{n} time steps of the full 4096^2 grid, FP64 oracle (OpenMP build, {threads} threads, "
+                      f"{dt:.1f} s)",
+            "single_thread": {"value": v1, "unit": METRIC, "cores": 1,
+                              "sample": f"{n1} time steps of the full 4096^2 grid, serial build ({dt1:.1f} s)"},
+            "host": host_info()}
 
 
 def run_reference(args, rank, world):
@@ -170,6 +245,8 @@ def run_reference(args, rank, world):
     import oracle
     from paper_1711_04471_gb300 import inputs
     inp = inputs.sw_wetdry(n=N_CELLS_SIDE, seed=1001)
+    oracle.use_openmp(True)       # the oracle's OpenMP build: all host cores, results bitwise equal to the serial one
+    threads = oracle.threads()
     s = oracle.SWState(inp.params(), inp.H, inp.eta0)
     for _ in range(args.warmup):
         s.run(1)
@@ -177,15 +254,18 @@ def run_reference(args, rank, world):
     for _ in range(args.steps):
         s.run(1)
     dt = time.perf_counter() - t0
+    oracle.use_openmp(False)
     cells = N_CELLS_SIDE ** 2 * args.steps
     value = cells / dt
-    sample = f"{args.steps} time steps of the full 4096^2 grid (1 model step per bench step), FP64, 1 thread"
+    sample = (f"{args.steps} time steps of the full 4096^2 grid (1 model step per bench step), FP64, "
+              f"{threads} threads")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": WORKLOAD, "grid": [N_CELLS_SIDE, N_CELLS_SIDE]},
-        "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": METRIC, "cores": threads, "kind": "oracle", "sample": sample,
+                         "host": host_info()},
         "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -209,7 +289,9 @@ def run_gbsw(args, rank, world, local):
     if args.blocking:
         sw.set_blocking(args.blocking)
     T = args.blocking or 3
-    launches_per_step = math.ceil(STEPS_PER_BENCH_STEP / T) + 2
+    fused_launches = math.ceil(STEPS_PER_BENCH_STEP / T)
+    whole = STEPS_PER_BENCH_STEP % T == 0       # every launch of the timed step fuses T time steps
+    launches_per_step = fused_launches + 2      # + the two volume-reduction kernels
 
     # ---- device-resident throughput (value) ----
     for _ in range(args.warmup):
@@ -238,7 +320,7 @@ def run_gbsw(args, rank, world, local):
     t_ms = start.elapsed_time(end)
     t_ms = max_over_ranks(t_ms, world)
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    fused_launch_ms = sum(step_ms) / (args.steps * math.ceil(STEPS_PER_BENCH_STEP / T))
+    fused_launch_ms = sum(step_ms) / (args.steps * fused_launches)
     value = cells * STEPS_PER_BENCH_STEP * args.steps * world / (t_ms * 1e-3)
 
     # ---- end to end through the public API with host buffers ----
@@ -267,9 +349,14 @@ def run_gbsw(args, rank, world, local):
     peak, peak_kind = _peaks()
     achieved_gbs = BYTES_PER_CELL_UPDATE * cells * T / (fused_launch_ms * 1e-3) / 1e9
     compulsory_gbs = BYTES_PER_CELL_UPDATE * cells / (fused_launch_ms * 1e-3) / 1e9
-    cpu_value, cpu_s = (None, None)
+    traffic, traffic_note = (args.traffic, "given on the command line") if args.traffic is not None else \
+        (ncu_traffic("sw_stream_kernel<3>") if T == 3 else (None, f"no ncu capture of T = {T}"))
+    cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        cpu_value, cpu_s = cpu_oracle_rate()
+        cpu = cpu_oracle_sw()
+    les = None
+    if world == 1 and not args.no_les:
+        les = les_object(args, local)
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
@@ -278,20 +365,19 @@ def run_gbsw(args, rank, world, local):
                    "steps_per_launch": T, "l2": "state 268 MB > 129 MB L2, no flush needed",
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": peak, "unit": "GB/s",
-                     "frac": achieved_gbs / peak,
-                     "traffic": args.traffic if args.traffic is not None else
-                     (TRAFFIC_SW_STREAM_T3 if T == 3 else None),
-                     "peak_kind": peak_kind, "kernel": "sw_stream_kernel",
+                     "frac": achieved_gbs / peak, "traffic": traffic, "traffic_note": traffic_note,
+                     "peak_kind": peak_kind, "kernel": f"sw_stream_kernel<{T}>",
                      "per_unit": f"{BYTES_PER_CELL_UPDATE} B/cell-update x {T} steps x {cells} cells per launch",
                      "compulsory_gbs": compulsory_gbs, "compulsory_frac": compulsory_gbs / peak,
-                     "launch_ms": fused_launch_ms},
-        "cpu_baseline": None if cpu_value is None else {
-            "value": cpu_value, "unit": METRIC, "cores": 1, "kind": "oracle",
-            "sample": f"10 time steps of the full 4096^2 grid, FP64 oracle, 1 thread ({cpu_s:.1f} s)"},
+                     "launch_ms": fused_launch_ms,
+                     "launch_ms_from": f"{fused_launches} launches per step, each fusing {T} time steps" if whole
+                     else f"{fused_launches} launches per step, the last one fusing {STEPS_PER_BENCH_STEP % T}"},
+        "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
         "volume_drift": (vols[-1][0] - vols[0][0]) / vols[0][0],
+        "les": les,
     }
     print(json.dumps(line), flush=True)
 
@@ -366,17 +452,23 @@ def run_ensemble(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
-def _les_cpu_sample(shape, solid, sor_iters=20):
-    """Oracle (FP64, one thread) on the full grid: one predictor pass and
-    sor_iters SOR iterations, timed separately."""
-    import ctypes as C
-
+def _les_cpu_sample(shape, solid, sor_iters=20, openmp=False):
+    """Oracle (FP64; its serial build on one thread, or its OpenMP build on
+    all host cores) on the full grid: one predictor pass and sor_iters SOR
+    iterations, timed separately."""
     import oracle
+    oracle.use_openmp(openmp)
+    try:
+        return _les_cpu_sample_run(shape, solid, sor_iters)
+    finally:
+        oracle.use_openmp(False)
+
+
+def _les_cpu_sample_run(shape, solid, sor_iters):
     from oracle import les as ol
     nx, ny, nz = shape
     Pm = ol.make_params(nx, ny, nz)
     st = ol.LESState(Pm, solid)
-    L = oracle.lib()
     t0 = time.perf_counter()
     ol.velnw(Pm, st.p, st.u, st.v, st.w)
     ol.bondv1(Pm, st.u, st.v, st.w)
@@ -393,79 +485,163 @@ def _les_cpu_sample(shape, solid, sor_iters=20):
     return t_pred, t_iter
 
 
-def run_les(args, rank, world, local, learned):
-    """UFLES 256x256x128 (20 % building cover), SOR omega 1.8 to a 1e-6
-    relative FP64 residual, 20 spin-up steps excluded.  With learned=True each
-    timed state is stepped twice: previous-pressure warm start and the U-Net."""
+LES_SHAPE = (256, 256, 128)
+
+
+def l2_copy_gbs(mb=24.0, reps=200):
+    """Copy bandwidth (read + write bytes) of a pair of buffers that fit in
+    L2 together (2 x 24 MB): the ceiling of a kernel whose working set stays
+    in L2 between launches.  Best of five timed loops of reps copies."""
+    import torch
+    n = int(mb * 1e6) // 4
+    a = torch.ones(n, dtype=torch.float32, device="cuda")
+    b = torch.empty_like(a)
+    for _ in range(20):
+        b.copy_(a)
+    best = 0.0
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            b.copy_(a)
+        e1.record()
+        torch.cuda.synchronize()
+        best = max(best, 2 * n * 4 * reps / (e0.elapsed_time(e1) * 1e-3) / 1e9)
+    return best
+
+
+def les_compare(args, solid, shape=LES_SHAPE, log=lambda *a: None):
+    """The UFLES step at the solver tolerance after args.les_spinup steps:
+    from each of args.les_steps states of a previous-pressure run, one step
+    with the previous pressure as warm start and one with the U-Net, both to
+    the same tolerance (device times from the step's own CUDA events).  Then
+    each run continues for args.les_e2e_steps steps timed end to end on the
+    host: les_step plus the read-back of the FP64 pressure to host memory."""
     import numpy as np
+
+    from paper_1711_04471_gb300.les import LES
+    from paper_1711_04471_gb300.unet import UNet
+    kw = dict(check_every=args.check_every, max_iter=400000)
+    names = ("u", "v", "w", "p", "fuo", "fvo", "fwo", "gu", "gv", "gw")
+    rows = []
+    with UNet(seed=0) as net, LES(*shape, solid, **kw) as ref, LES(*shape, solid, **kw) as trial:
+        net.set_params(np.load(args.weights))
+        ref.step(args.les_spinup, stats=False)
+        trial.set_warm_start(net)
+        for _ in range(args.les_steps):
+            state = {n: ref.get(n) for n in names}
+            count = ref.step_count
+            for n in names:
+                trial.set(n, state[n])
+            trial.step_count = count
+            a = ref.step(1)[0]
+            b = trial.step(1)[0]
+            rows.append(dict(step=count + 1, plain_iters=a["iters"], nn_iters=b["iters"],
+                             plain_ms=a["ms_predictor"] + a["ms_solve"], plain_pred_ms=a["ms_predictor"],
+                             plain_solve_ms=a["ms_solve"], plain_res=a["rel_res"], plain_status=a["status"],
+                             nn_ms=b["ms_predictor"] + b["ms_guess"] + b["ms_solve"], nn_guess_ms=b["ms_guess"],
+                             nn_solve_ms=b["ms_solve"], nn_res=b["rel_res"], nn_status=b["status"]))
+            log(rows[-1])
+        e2e = {}
+        for name, g in (("plain", ref), ("learned", trial)):
+            g.step(1, stats=False)
+            t0 = time.perf_counter()
+            for _ in range(args.les_e2e_steps):
+                g.step(1)
+                p = g.get("p")
+            e2e[name] = {"value": (time.perf_counter() - t0) / args.les_e2e_steps * 1e3, "unit": "ms/step",
+                         "h2d_bytes_per_step": 0, "d2h_bytes_per_step": int(p.nbytes),
+                         "what": f"les_step (stats read back) + FP64 pressure to host, {args.les_e2e_steps} steps"}
+    return rows, e2e
+
+
+def les_object(args, local):
+    """The second half of the metric: UFLES step time at a 1e-6 residual,
+    learned vs previous-pressure warm start (see les_compare), with the SOR
+    sweep against the L2 copy bandwidth and the FP64 oracle on the host."""
+    import torch
+
+    from paper_1711_04471_gb300 import inputs
+    shape = LES_SHAPE
+    solid = inputs.les_buildings(*shape, dx=4.0, seed=args.les_seed)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    t_wall = time.perf_counter()
+    rows, e2e = les_compare(args, solid, shape)
+    t_wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    l2 = l2_copy_gbs()
+    n = len(rows)
+    mean = lambda k: sum(r[k] for r in rows) / n
+    cells = shape[0] * shape[1] * shape[2]
+    it_plain = mean("plain_iters")
+    per_iter_s = mean("plain_solve_ms") * 1e-3 / max(it_plain, 1)
+    ach = 12.0 * cells / per_iter_s / 1e9      # 12 B/cell/iteration: correction in + out, residual in
+    traffic, note = ncu_traffic("sor_iteration_256x256x128")
+    out = {
+        "workload": f"UFLES 256x256x128, dx 4 m, dt 0.025 s, 20 % building cover (building seed {args.les_seed}), "
+                    f"SOR omega 1.8 to a 1e-6 relative FP64 residual checked every {args.check_every} iterations; "
+                    f"{args.les_spinup} spin-up steps, then {n} states compared",
+        "metric": "LES step time at 1e-6 residual, learned vs previous-pressure warm start",
+        "unit": "ms/step", "higher_is_better": False, "dtype": "f32 sweeps, f64 pressure and norms",
+        "plain": {"ms_per_step": mean("plain_ms"), "sor_iters_per_step": it_plain,
+                  "predictor_ms": mean("plain_pred_ms"), "solve_ms": mean("plain_solve_ms"),
+                  "max_rel_res": max(r["plain_res"] for r in rows),
+                  "all_converged": all(r["plain_status"] == 0 for r in rows)},
+        "learned": {"ms_per_step": mean("nn_ms"), "sor_iters_per_step": mean("nn_iters"),
+                    "guess_ms": mean("nn_guess_ms"), "solve_ms": mean("nn_solve_ms"),
+                    "max_rel_res": max(r["nn_res"] for r in rows),
+                    "all_converged": all(r["nn_status"] == 0 for r in rows)},
+        "e2e": e2e, "wall_s": t_wall, "clocks": clk,
+        "roofline": {"bound": "l2", "kernel": "SOR iteration (red + black half-sweep) inside the solve graph",
+                     "achieved": ach, "peak": l2, "unit": "GB/s", "frac": ach / l2,
+                     "peak_kind": "measured in this run: L2-resident copy (2 x 24 MB buffers, torch copy_, best of 5)",
+                     "per_unit": f"12 B/cell/iteration x {cells} cells (solve time / iterations, checks included)",
+                     "traffic": traffic, "traffic_note": note or "DRAM bytes per iteration, warm L2",
+                     "hbm_frac": ach / _peaks()[0]},
+        "rows": rows,
+    }
+    out["learned"]["speedup"] = out["plain"]["ms_per_step"] / out["learned"]["ms_per_step"]
+    if not args.no_cpu_baseline:
+        cpu = {}
+        for omp in (False, True):
+            t_pred, t_iter = _les_cpu_sample(shape, solid, openmp=omp)
+            cpu[omp] = (t_pred + it_plain * t_iter) * 1e3
+        import oracle
+        th = oracle.threads()
+        out["cpu_baseline"] = {
+            "value": cpu[True], "unit": "ms/step", "cores": th, "kind": "oracle",
+            "sample": f"one predictor pass + 20 SOR iterations on the full grid (FP64, OpenMP build, {th} threads), "
+                      f"step time extrapolated to the plain run's {it_plain:.0f} iterations",
+            "single_thread": {"value": cpu[False], "unit": "ms/step", "cores": 1}, "host": host_info()}
+    return out
+
+
+
+def run_les(args, rank, world, local, learned):
+    """UFLES 256x256x128 on its own line: the les object of the default line
+    with args.steps compared states; value = the learned (les-nn) or the
+    previous-pressure (les) warm start's device ms per step."""
     import torch
 
     import paper_1711_04471_gb300 as P
-    from paper_1711_04471_gb300 import inputs
-    from paper_1711_04471_gb300.les import LES
     P.build()
     torch.cuda.set_device(local)
-    shape = (256, 256, 128)
-    solid = inputs.les_buildings(*shape, dx=4.0, seed=args.les_seed)
-    kw = dict(check_every=args.check_every, max_iter=400000)
-    rows = []
-    clocks = ClockSampler(torch.cuda.current_device())
-    clocks.start()
-    if learned:
-        from paper_1711_04471_gb300 import train_unet
-        from paper_1711_04471_gb300.unet import UNet
-        net = UNet(seed=0)
-        net.set_params(np.load(args.weights))
-        rows = train_unet.compare_warm_starts(net, shape=shape, seed=args.les_seed, spinup=args.spinup,
-                                              steps=args.steps, log=lambda *a: None, **kw)
-        net.close()
-        t_plain = sum(r["plain_ms"] for r in rows) / len(rows)
-        t_nn = sum(r["nn_ms"] for r in rows) / len(rows)
-    else:
-        with LES(*shape, solid, **kw) as g:
-            g.step(args.spinup, stats=False)
-            st = g.step(args.steps)
-        rows = [dict(plain_iters=a["iters"], plain_ms=a["ms_predictor"] + a["ms_solve"],
-                     pred_ms=a["ms_predictor"], solve_ms=a["ms_solve"], res=a["rel_res"]) for a in st]
-        t_plain = sum(r["plain_ms"] for r in rows) / len(rows)
-    clk = clocks.stop()
+    args.les_steps = args.steps
+    args.les_spinup = args.spinup
+    obj = les_object(args, local)
     if rank != 0:
         return
-    cells = shape[0] * shape[1] * shape[2]
-    iters = sum(r["plain_iters"] for r in rows) / len(rows)
-    peak, peak_kind = _peaks()
-    solve_ms = (sum(r.get("solve_ms", r["plain_ms"]) for r in rows) / len(rows))
-    per_iter_s = solve_ms * 1e-3 / max(iters, 1)
-    ach = 12.0 * cells / per_iter_s / 1e9      # 12 B/cell/iteration: correction in+out, residual in
-    t_pred, t_iter = _les_cpu_sample(shape, solid) if (world == 1 and not args.no_cpu_baseline) else (None, None)
+    key = "learned" if learned else "plain"
     line = {"metric": "LES step time at 1e-6 residual" + (" (learned warm start)" if learned else ""),
-            "value": t_nn if learned else t_plain, "unit": "ms/step", "n_gpus": world, "steps": args.steps,
-            "warmup": args.spinup, "ms_per_step": t_nn if learned else t_plain, "higher_is_better": False,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32 sweeps, f64 pressure and norms",
-            "data": "synthetic",
-            "config": {"workload": f"UFLES 256x256x128, dx 4 m, dt 0.025 s, 20 % building cover (building seed "
-                                   f"{args.les_seed}), SOR omega 1.8, "
-                                   "tol 1e-6 (FP64), warm start " + ("U-Net vs previous pressure" if learned
-                                                                     else "previous pressure"),
-                       "spinup_steps": args.spinup, "check_every": args.check_every,
-                       "l2": f"e and r (71 MB) stay in the {_l2_mb():.0f} MB L2 between sweeps; that reuse is the "
-                             "method's own"},
-            "clocks": clk,
-            "sor_iters_per_step": iters,
-            "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                         "traffic": TRAFFIC_SOR_ITER_256 if shape == (256, 256, 128) else None,
-                         "traffic_unit": "bytes per SOR iteration (two half-sweeps), warm L2",
-                         "peak_kind": peak_kind, "kernel": "sor_sweep_kernel",
-                         "per_unit": "12 B/cell/iteration x 8388608 cells (solve time / iterations)"},
-            "cpu_baseline": None if t_pred is None else {
-                "value": (t_pred + iters * t_iter) * 1e3, "unit": "ms/step", "cores": 1, "kind": "oracle",
-                "sample": f"one predictor pass + 20 SOR iterations on the full grid (FP64, 1 thread), "
-                          f"step time extrapolated to {iters:.0f} iterations"},
-            "rows": rows}
-    if learned:
-        line["plain"] = {"ms_per_step": t_plain, "sor_iters_per_step": iters}
-        line["learned"] = {"ms_per_step": t_nn, "sor_iters_per_step": sum(r["nn_iters"] for r in rows) / len(rows),
-                           "guess_ms": sum(r["nn_guess_ms"] for r in rows) / len(rows)}
+            "value": obj[key]["ms_per_step"], "unit": "ms/step", "n_gpus": world, "steps": args.steps,
+            "warmup": args.spinup, "ms_per_step": obj[key]["ms_per_step"], "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": obj["dtype"], "data": "synthetic",
+            "config": {"workload": obj["workload"], "l2": f"e and r (71 MB) stay in the {_l2_mb():.0f} MB L2 "
+                                                          "between sweeps; that reuse is the method's own"},
+            "clocks": obj["clocks"], "sor_iters_per_step": obj[key]["sor_iters_per_step"],
+            "roofline": obj["roofline"], "cpu_baseline": obj.get("cpu_baseline"), "e2e": obj["e2e"][key],
+            "plain": obj["plain"], "learned": obj["learned"], "rows": obj["rows"]}
     print(json.dumps(line), flush=True)
 
 
@@ -487,16 +663,21 @@ def run_sw_paper(args, rank, world, local):
             g.step(300)
             g.volume()
             t = _timed_region(lambda: (g.step(10000), g.volume()), world)
-        cpu = None
+        cpu = {}
         if not args.no_cpu_baseline:
             import oracle
-            o = oracle.SWState(inp.params(), inp.H, inp.eta0)
-            steps = max(1, int(2e7 // (n * n)))
-            t0 = time.perf_counter()
-            o.run(steps)
-            cpu = n * n * steps / (time.perf_counter() - t0)
+            for omp in (False, True):
+                oracle.use_openmp(omp)
+                o = oracle.SWState(inp.params(), inp.H, inp.eta0)
+                steps = max(1, int((8e7 if omp else 2e7) // (n * n)))
+                t0 = time.perf_counter()
+                o.run(steps)
+                cpu[omp] = n * n * steps / (time.perf_counter() - t0)
+                oracle.use_openmp(False)
+            cpu["threads"] = oracle.threads()
         res.append({"n": n, "seconds_10000_steps": t, "cell_updates_per_s": n * n * 10000 / t,
-                    "oracle_cell_updates_per_s_1thread": cpu})
+                    "oracle_cell_updates_per_s_1thread": cpu.get(False),
+                    "oracle_cell_updates_per_s_all_cores": cpu.get(True), "oracle_threads": cpu.get("threads")})
     if rank != 0:
         return
     big = res[-1]
@@ -568,10 +749,16 @@ def run_les_paper(args, rank, world, local):
         return
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        t_pred, t_iter = _les_cpu_sample(shape, solid)
-        cpu = {"value": (t_pred + 50 * t_iter) * 1e3, "unit": "ms/step", "cores": 1, "kind": "oracle",
-               "sample": "one predictor pass + 20 SOR iterations on the full 300x300x90 grid (FP64, 1 thread), "
-                         "step time for 50 iterations", "predictor_ms": t_pred * 1e3, "sor_iteration_ms": t_iter * 1e3}
+        import oracle
+        t_pred, t_iter = _les_cpu_sample(shape, solid, openmp=True)
+        s_pred, s_iter = _les_cpu_sample(shape, solid, openmp=False)
+        th = oracle.threads()
+        cpu = {"value": (t_pred + 50 * t_iter) * 1e3, "unit": "ms/step", "cores": th, "kind": "oracle",
+               "sample": f"one predictor pass + 20 SOR iterations on the full 300x300x90 grid (FP64, OpenMP build, "
+                         f"{th} threads), step time for 50 iterations", "predictor_ms": t_pred * 1e3,
+               "sor_iteration_ms": t_iter * 1e3,
+               "single_thread": {"value": (s_pred + 50 * s_iter) * 1e3, "unit": "ms/step", "cores": 1},
+               "host": host_info()}
     print(json.dumps({"metric": "LES step time, 50 SOR iterations (paper setup)", "value": pred + solve,
                       "unit": "ms/step", "n_gpus": world, "steps": args.steps, "warmup": args.spinup,
                       "ms_per_step": pred + solve, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
@@ -582,10 +769,68 @@ def run_les_paper(args, rank, world, local):
                       "final_rel_res": sum(a["rel_res"] for a in st) / len(st)}), flush=True)
 
 
+def run_poisson(args, rank, world, local):
+    """The pressure solve alone (poisson_solve) on a seeded random right-hand
+    side of the --grid size: --iters iterations of the paper's fixed-count
+    SOR launched directly (--mode fixed, the form an ncu launch list
+    resolves per half-sweep), or the tolerance-driven conditional graph with
+    a check every 50 iterations and an unreachable tolerance (--mode graph).
+    Prints the time per iteration, setup included."""
+    import torch
+
+    import paper_1711_04471_gb300 as P
+    from paper_1711_04471_gb300.les import poisson_solve
+    P.build()
+    torch.cuda.set_device(local)
+    nx, ny, nz = args.grid
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    b = torch.randn((nz, ny, nx), device="cuda", generator=gen) * 1e-3
+    p = torch.zeros_like(b)
+    tol = -1.0 if args.mode == "fixed" else 1e-30
+    poisson_solve(p.clone(), b, 4.0, tol=tol, max_iter=min(args.iters, 50), check_every=50)    # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st, it, rr = poisson_solve(p, b, 4.0, tol=tol, max_iter=args.iters, check_every=50)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    if rank == 0:
+        print(json.dumps({"metric": "SOR iteration time (poisson_solve alone)", "value": dt / max(it, 1) * 1e6,
+                          "unit": "us/iteration", "higher_is_better": False, "grid": [nx, ny, nz],
+                          "mode": args.mode, "iterations": it, "rel_res": rr, "status": st}), flush=True)
+
+
+def run_unet(args, rank, world, local):
+    """U-Net inference alone (unet_forward) on a random (1, D, H, W, 2)
+    input of the --grid size (given as W H D), --iters repetitions."""
+    import torch
+
+    import paper_1711_04471_gb300 as P
+    from paper_1711_04471_gb300.unet import UNet
+    P.build()
+    torch.cuda.set_device(local)
+    W, H, D = args.grid
+    x = torch.randn((1, D, H, W, 2), device="cuda")
+    with UNet(seed=0) as net:
+        net.forward(x)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.iters):
+            net.forward(x)
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / args.iters
+    if rank == 0:
+        print(json.dumps({"metric": "U-Net forward time", "value": dt * 1e3, "unit": "ms", "higher_is_better": False,
+                          "input": [1, D, H, W, 2], "reps": args.iters}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="sw4096", choices=["sw4096", "sw64", "ensemble", "les", "les-nn", "sw-paper",
-                                                                 "les-paper"])
+                                                                 "les-paper", "poisson", "unet"])
+    ap.add_argument("--grid", type=int, nargs=3, default=[256, 256, 128],
+                    help="poisson / unet workloads: NX NY NZ")
+    ap.add_argument("--iters", type=int, default=200, help="poisson: SOR iterations; unet: repetitions")
+    ap.add_argument("--mode", default="fixed", choices=["fixed", "graph"], help="poisson workload")
     ap.add_argument("--spinup", type=int, default=20)
     ap.add_argument("--weights", default=os.path.join(ROOT, "paper_1711_04471_gb300", "data", "unet_warmstart.npy"))
     ap.add_argument("--gpus", type=int, default=1)
@@ -596,6 +841,10 @@ def main():
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu DRAM bytes per fused launch, if captured for this kernel version")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-les", action="store_true", help="default workload: leave out the UFLES object")
+    ap.add_argument("--les-spinup", type=int, default=20, help="UFLES object: spin-up steps before the comparison")
+    ap.add_argument("--les-steps", type=int, default=10, help="UFLES object: compared states")
+    ap.add_argument("--les-e2e-steps", type=int, default=3, help="UFLES object: steps per end-to-end timing")
     ap.add_argument("--check-every", type=int, default=500,
                     help="les workloads: SOR iterations between FP64 residual checks")
     ap.add_argument("--les-seed", type=int, default=1003,
@@ -615,6 +864,10 @@ def main():
         run_sw_paper(args, rank, world, local)
     elif args.workload == "les-paper":
         run_les_paper(args, rank, world, local)
+    elif args.workload == "poisson":
+        run_poisson(args, rank, world, local)
+    elif args.workload == "unet":
+        run_unet(args, rank, world, local)
     elif args.workload in ("les", "les-nn"):
         run_les(args, rank, world, local, learned=args.workload == "les-nn")
     else:

@@ -465,9 +465,10 @@ gbsw_status warm_start_apply(int nx, int ny, int nz, int f, const float *out, do
  *
  * The partial sums live in a fixed 24 KB array inside the library (one
  * per GPU, held until the process exits), so no call allocates anything.
- * The first call on a device looks up that array's device address (a
- * one-time set-up with that device current); make that first call before
- * any stream capture.  All calls share the array and each call overwrites
+ * The first call in a device's CUDA context looks up that array's device
+ * address (a set-up done once per device with that device current, and
+ * again if the device's context is destroyed and re-created); make that
+ * first call before any stream capture.  All calls share the array and each call overwrites
  * it completely: calls whose kernels can overlap on the GPU (other streams
  * or host threads) race and must be serialised by the caller.
  */

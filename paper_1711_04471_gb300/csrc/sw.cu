@@ -356,6 +356,7 @@ void sw_destroy(gbsw_sw *s)
 // all calls share it: calls whose kernels overlap on the GPU (different
 // streams, or different host threads) race on it.
 // ---------------------------------------------------------------------------
+#include <cuda.h>
 #include <mutex>
 
 static __device__ __align__(256) double g_sw_volume_scratch[SW_VOL_BLOCKS * 3];
@@ -364,23 +365,58 @@ namespace {
 
 constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mutex;
-double *g_scratch_addr[kMaxDevices];  // device address of g_sw_volume_scratch, per device
+struct ScratchAddr {
+    unsigned long long ctx_id;  // CUDA context the address belongs to (IDs are never reused in a process)
+    double *addr;               // device address of g_sw_volume_scratch in that context
+};
+ScratchAddr g_scratch_addr[kMaxDevices];
 
-// Device address of the scratch array on the current device, looked up
-// once per device.  In host code the array's name is only a host-side
-// stand-in, so the address must come from cudaGetSymbolAddress.
+// Device address of the scratch array in the current device's context.  In
+// host code the array's name is only a host-side stand-in, so the address
+// comes from cudaGetSymbolAddress, looked up on the first call in each
+// context: once per device, and again if that device's context was
+// destroyed and re-created (the module is then loaded anew, at a possibly
+// different address).
 gbsw_status volume_scratch(double **out)
 {
     int dev = 0;
     GBSW_CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kMaxDevices) return GBSW_ERR_ARG;
     std::lock_guard<std::mutex> lock(g_scratch_mutex);
-    if (!g_scratch_addr[dev]) {
+    // driver calls through the runtime's entry-point query, so that loading
+    // the library does not need the driver library on hosts without a GPU
+    using GetCurrentFn = CUresult (*)(CUcontext *);
+    using GetIdFn = CUresult (*)(CUcontext, unsigned long long *);
+    static GetCurrentFn get_current = nullptr;
+    static GetIdFn get_id = nullptr;
+    if (!get_current || !get_id) {
+        void *a = nullptr, *b = nullptr;
+        cudaDriverEntryPointQueryResult qa, qb;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa) != cudaSuccess ||
+            qa != cudaDriverEntryPointSuccess ||
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb) != cudaSuccess ||
+            qb != cudaDriverEntryPointSuccess)
+            return GBSW_ERR_CUDA;
+        get_current = (GetCurrentFn)a;
+        get_id = (GetIdFn)b;
+    }
+    CUcontext ctx = nullptr;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx) {
+        // no current context yet: the runtime creates the primary one here
         void *p = nullptr;
         GBSW_CUDA_TRY(cudaGetSymbolAddress(&p, g_sw_volume_scratch));
-        g_scratch_addr[dev] = (double *)p;
+        if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return GBSW_ERR_CUDA;
     }
-    *out = g_scratch_addr[dev];
+    unsigned long long id = 0;
+    if (get_id(ctx, &id) != CUDA_SUCCESS) return GBSW_ERR_CUDA;
+    ScratchAddr &e = g_scratch_addr[dev];
+    if (!e.addr || e.ctx_id != id) {
+        void *p = nullptr;
+        GBSW_CUDA_TRY(cudaGetSymbolAddress(&p, g_sw_volume_scratch));
+        e.addr = (double *)p;
+        e.ctx_id = id;
+    }
+    *out = e.addr;
     return GBSW_OK;
 }
 

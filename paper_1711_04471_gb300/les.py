@@ -137,35 +137,3 @@ def warm_start_apply(out, scale: float, p, f: int, stream=None):
     assert tuple(out.shape) == (nz // f, ny // f, nx // f)
     N.check(N.lib().warm_start_apply(nx, ny, nz, int(f), N.tensor_ptr(out, "float32"), float(scale),
                                      N.tensor_ptr(p, "float64"), N.stream_handle(stream)), "warm_start_apply")
-
-
-def _main():
-    """Time the pressure solve alone: python -m paper_1711_04471_gb300.les NX NY NZ ITERS [MODE]
-    on a seeded random right-hand side (MODE fixed: ITERS direct-launch
-    iterations, the paper's fixed-count SOR; graph: the conditional graph
-    with a check every 50 iterations and an unreachable tolerance)."""
-    import sys
-    import time
-
-    import torch
-
-    from . import build
-    build()
-    nx, ny, nz, iters = (int(a) for a in sys.argv[1:5])
-    mode = sys.argv[5] if len(sys.argv) > 5 else "fixed"
-    gen = torch.Generator(device="cuda").manual_seed(0)
-    b = torch.randn((nz, ny, nx), device="cuda", generator=gen) * 1e-3
-    p = torch.zeros_like(b)
-    tol = -1.0 if mode == "fixed" else 1e-30
-    poisson_solve(p.clone(), b, 4.0, tol=tol, max_iter=min(iters, 50), check_every=50)    # warm-up
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    st, it, rr = poisson_solve(p, b, 4.0, tol=tol, max_iter=iters, check_every=50)
-    torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
-    print(f"poisson {nx}x{ny}x{nz} {mode}: {it} iterations in {dt * 1e3:.2f} ms ({dt / max(it, 1) * 1e6:.2f} us "
-          f"per iteration incl. setup), relative residual {rr:.4e}")
-
-
-if __name__ == "__main__":
-    _main()

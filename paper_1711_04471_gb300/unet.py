@@ -92,30 +92,3 @@ class UNet:
 
     def __exit__(self, *exc):
         self.close()
-
-
-def _main():
-    """Time inference: python -m paper_1711_04471_gb300.unet D H W [reps]."""
-    import sys
-    import time
-
-    import torch
-
-    from . import build
-    build()
-    D, H, W = (int(a) for a in sys.argv[1:4])
-    reps = int(sys.argv[4]) if len(sys.argv) > 4 else 10
-    x = torch.randn((1, D, H, W, 2), device="cuda")
-    with UNet(seed=0) as net:
-        net.forward(x)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(reps):
-            net.forward(x)
-        torch.cuda.synchronize()
-        dt = (time.perf_counter() - t0) / reps
-    print(f"U-Net forward {D}x{H}x{W}: {dt * 1e3:.3f} ms")
-
-
-if __name__ == "__main__":
-    _main()
