@@ -488,26 +488,17 @@ def _les_cpu_sample_run(shape, solid, sor_iters):
 LES_SHAPE = (256, 256, 128)
 
 
-def l2_copy_gbs(mb=24.0, reps=200):
-    """Copy bandwidth (read + write bytes) of a pair of buffers that fit in
-    L2 together (2 x 24 MB): the ceiling of a kernel whose working set stays
-    in L2 between launches.  Best of five timed loops of reps copies."""
-    import torch
-    n = int(mb * 1e6) // 4
-    a = torch.ones(n, dtype=torch.float32, device="cuda")
-    b = torch.empty_like(a)
-    for _ in range(20):
-        b.copy_(a)
-    best = 0.0
-    for _ in range(5):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(reps):
-            b.copy_(a)
-        e1.record()
-        torch.cuda.synchronize()
-        best = max(best, 2 * n * 4 * reps / (e0.elapsed_time(e1) * 1e-3) / 1e9)
-    return best
+def l2_copy_gbs(mb=32.0, passes=64):
+    """Copy bandwidth (read + write bytes) of two buffers that fit in L2
+    together (2 x 32 MB): the ceiling of a kernel whose working set stays in
+    L2 between launches.  The library's probe copies `passes` times inside
+    one launch, so launch gaps do not count; best of five launches."""
+    import ctypes as C
+
+    from paper_1711_04471_gb300 import _native as N
+    g = C.c_double()
+    N.check(N.lib().gbsw_measure_l2_copy(int(mb * 1e6) // 16 * 16, passes, C.byref(g)), "gbsw_measure_l2_copy")
+    return g.value
 
 
 def les_compare(args, solid, shape=LES_SHAPE, log=lambda *a: None):
@@ -595,7 +586,8 @@ def les_object(args, local):
         "e2e": e2e, "wall_s": t_wall, "clocks": clk,
         "roofline": {"bound": "l2", "kernel": "SOR iteration (red + black half-sweep) inside the solve graph",
                      "achieved": ach, "peak": l2, "unit": "GB/s", "frac": ach / l2,
-                     "peak_kind": "measured in this run: L2-resident copy (2 x 24 MB buffers, torch copy_, best of 5)",
+                     "peak_kind": "measured in this run: L2-resident copy (gbsw_measure_l2_copy, 2 x 32 MB buffers, "
+                                  "64 passes per launch, best of 5)",
                      "per_unit": f"12 B/cell/iteration x {cells} cells (solve time / iterations, checks included)",
                      "traffic": traffic, "traffic_note": note or "DRAM bytes per iteration, warm L2",
                      "hbm_frac": ach / _peaks()[0]},
@@ -823,10 +815,40 @@ def run_unet(args, rank, world, local):
                           "input": [1, D, H, W, 2], "reps": args.iters}), flush=True)
 
 
+def run_unet_train(args, rank, world, local):
+    """U-Net training alone (unet_train_step: forward, backward with the
+    tcgen05 weight gradients, Adam) on the warm-start training batch: 32
+    samples of the coarse grid (--grid W H D, default 16 16 8), --iters
+    steps after 5 warm-up steps."""
+    import torch
+
+    import paper_1711_04471_gb300 as P
+    from paper_1711_04471_gb300.unet import UNet
+    P.build()
+    torch.cuda.set_device(local)
+    W, H, D = args.grid if args.grid != [256, 256, 128] else (16, 16, 8)
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.randn((32, D, H, W, 2), device="cuda", generator=gen)
+    t = torch.randn((32, D, H, W), device="cuda", generator=gen) * 0.1
+    with UNet(seed=0) as net:
+        for _ in range(5):
+            net.train_step(x, t, 1e-4)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.iters):
+            net.train_step(x, t, 1e-4)
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / args.iters
+    if rank == 0:
+        print(json.dumps({"metric": "U-Net training step time", "value": dt * 1e3, "unit": "ms",
+                          "higher_is_better": False, "batch": [32, D, H, W, 2], "steps": args.iters,
+                          "note": "host-timed, loss read back every step"}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="sw4096", choices=["sw4096", "sw64", "ensemble", "les", "les-nn", "sw-paper",
-                                                                 "les-paper", "poisson", "unet"])
+                                                                 "les-paper", "poisson", "unet", "unet-train"])
     ap.add_argument("--grid", type=int, nargs=3, default=[256, 256, 128],
                     help="poisson / unet workloads: NX NY NZ")
     ap.add_argument("--iters", type=int, default=200, help="poisson: SOR iterations; unet: repetitions")
@@ -868,6 +890,8 @@ def main():
         run_poisson(args, rank, world, local)
     elif args.workload == "unet":
         run_unet(args, rank, world, local)
+    elif args.workload == "unet-train":
+        run_unet_train(args, rank, world, local)
     elif args.workload in ("les", "les-nn"):
         run_les(args, rank, world, local, learned=args.workload == "les-nn")
     else:

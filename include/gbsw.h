@@ -54,6 +54,18 @@ int gbsw_version(void);
  * if none). */
 const char *gbsw_last_error(void);
 
+/*
+ * Measurement: copy bandwidth of data that stays in L2.  Copies one device
+ * buffer of `bytes` bytes (>= 1 MiB, a multiple of 16) onto another,
+ * `passes` times inside one launch of one wave of blocks, and writes the
+ * best of five timed launches (after one that brings both buffers into L2)
+ * to *gbs in GB/s, counting read and write bytes.  With 2 x bytes well
+ * below the L2 size this is the ceiling of a kernel whose working set stays
+ * in L2 (the SOR sweeps of the pressure solve, Sec. 6.3.1 "press").
+ * Allocates and frees its buffers; synchronous on the default stream.
+ */
+gbsw_status gbsw_measure_l2_copy(long long bytes, int passes, double *gbs);
+
 /* Self-test of the bounded device-side waits (the paper has no
  * counterpart).  which = 0 waits on an mbarrier phase that never completes
  * for `budget` clock cycles, which = 1 spins on a flag that is never set
@@ -344,21 +356,80 @@ gbsw_status poisson_solve(int nx, int ny, int nz, double dx, float *p, const flo
  * ---------------------------------------------------------------------- */
 
 /*
- * One 3x3x3 convolution with zero padding (operator-level entry point).
- *   x     device, nsamples*D*H*W*cin FP32, channels last (rounded to BF16)
- *   w     device, 27*cout*cin FP32, w[tap][co][ci] with tap = (dz+1)*9 +
- *         (dy+1)*3 + (dx+1) for input offsets dz, dy, dx (rounded to BF16)
- *   bias  device, cout FP32 (epilogue 0 only)
+ * Operator-level entry points: each runs one of the network's kernels on
+ * dense FP32 device tensors (nsamples, D, H, W, C), channels last, so that
+ * it can be compared with an FP64 reference on its own.  Inputs are
+ * rounded to BF16 (nearest even) as the network stores its activations;
+ * results are the kernels' FP32 values.  Geometry rule of the tcgen05
+ * convolutions: W a power of two or a multiple of 128; with m =
+ * 128/min(W, 128), H a multiple of m, or H a power of two below m with
+ * W*H >= 16 (a tile then spans m/H planes).  Each call allocates and frees
+ * temporary device buffers and is synchronous on `stream`; bad sizes or
+ * NULL pointers return GBSW_ERR_ARG.
+ */
+
+/*
+ * One 3x3x3 convolution with zero padding:
+ *   x     nsamples*D*H*W*cin, w 27*cout*cin with w[tap][co][ci], tap =
+ *         (dz+1)*9 + (dy+1)*3 + (dx+1) for input offsets dz, dy, dx (both
+ *         rounded to BF16), bias cout FP32 (epilogue 0 only)
  *   epilogue 0: y = max(conv + bias, 0); 1: y = conv; 2: y = conv where
- *         mask > 0, else 0 (mask: device FP32, same shape as y)
- *   y     device, nsamples*D*H*W*cout FP32 (the FP32 accumulator, unrounded)
- * cin, cout in {16, 32, 64} (pairs used by the network); W a power of two
- * or a multiple of 128.  With m = 128/min(W, 128): H a multiple of m, or
- * H a power of two below m with W*H >= 16 (a tile then spans m/H planes).
- * Synchronous; allocates a temporary BF16 copy of x and the packed weights.
+ *         mask > 0, else 0 (mask: FP32, same shape as y)
+ *   y     nsamples*D*H*W*cout FP32 (the FP32 accumulator)
+ * (cin, cout) one of the network's pairs, (16|32|64, 16|32|64) but not
+ * (64, 64), or cin = 2, which runs zero-padded to 16 as the first layer
+ * does.
  */
 gbsw_status unet_conv3d(int nsamples, int D, int H, int W, int cin, int cout, const float *x, const float *w,
                         const float *bias, int epilogue, const float *mask, float *y, void *stream);
+
+/*
+ * Backward-data of that convolution (the tcgen05 kernel with the flipped,
+ * transposed weight pack): gx[v][ci] = sum over taps and co of
+ * gy[v - off(tap)][co] w[tap][co][ci], zero outside the sample; with mask
+ * non-NULL (FP32, shape of gx) gx = 0 where mask <= 0.  gy
+ * nsamples*D*H*W*cout, w 27*cout*cin, gx nsamples*D*H*W*cin.  (cout, cin)
+ * must be a pair unet_conv3d accepts with cin >= 16.
+ */
+gbsw_status unet_conv3d_bwd_data(int nsamples, int D, int H, int W, int cin, int cout, const float *gy,
+                                 const float *w, const float *mask, float *gx, void *stream);
+
+/*
+ * Weight and bias gradients of that convolution on the tensor cores:
+ * dw[tap][co][ci] = sum_v gy[v][co] x[v + off(tap)][ci] (zero outside the
+ * sample), db[co] = sum_v gy[v][co]; dw (27*cout*cin) and db (cout) are
+ * overwritten.  x nsamples*D*H*W*cin, gy nsamples*D*H*W*cout.  (cin, cout)
+ * one of (2|16, 16), (16, 32), (32, 16|32|64), (64, 16|32): the network's
+ * layers.
+ */
+gbsw_status unet_conv3d_bwd_weight(int nsamples, int D, int H, int W, int cin, int cout, const float *x,
+                                   const float *gy, float *dw, float *db, void *stream);
+
+/*
+ * The glue between the convolutions, C in {8, 16, ..., 64}:
+ *   op 0  out (n, D/2, H/2, W/2, C) = 2x2x2 average of a (n, D, H, W, C)
+ *   op 1  out (n, 2D, 2H, 2W, C) = nearest upsampling of a (n, D, H, W, C)
+ *   op 2  out (n, D, H, W, C) = sum of the 8 children in a (n, 2D, 2H, 2W, C)
+ *         (the adjoint of op 1)
+ *   op 3  out (n, D, H, W, C) = (a + b / 8 at the parent cell) * [c > 0],
+ *         a, c (n, D, H, W, C), b (n, D/2, H/2, W/2, C): the gradient of a
+ *         ReLU output that feeds both a concatenation and a pool
+ * out is rounded to BF16 as the network stores it.  D, H, W even for ops 0
+ * and 3; b, c used by op 3 only.
+ */
+gbsw_status unet_glue(int op, int nsamples, int D, int H, int W, int C, const float *a, const float *b,
+                      const float *c, float *out, void *stream);
+
+/*
+ * The 1x1 head and the MSE loss: out[v] = hb + sum_c d1[v][c] hw[c]
+ * (d1 nvox*16, rounded to BF16; hw 16, hb 1 FP32).  With target (nvox)
+ * non-NULL also the backward pass of L = mean (out - target)^2:
+ * *loss = L (FP64), g_hw[c] = sum_v dL/dout_v d1[v][c], *g_hb = sum_v
+ * dL/dout_v, g_d1[v][c] = dL/dout_v hw[c] where d1[v][c] > 0 else 0
+ * (rounded to BF16).  1 <= nvox <= 2^30.
+ */
+gbsw_status unet_head(long long nvox, const float *d1, const float *hw, const float *hb, const float *target,
+                      float *out, float *g_hw, float *g_hb, float *g_d1, double *loss, void *stream);
 
 typedef struct gbsw_unet gbsw_unet;
 

@@ -39,6 +39,10 @@ def declare(L, sig):
     sig(L, "sw_batch_autotune", C.c_int, [vp, C.c_int, C.c_char_p, ip, ip])
     sig(L, "sw_batch_destroy", None, [vp])
     sig(L, "unet_conv3d", C.c_int, [C.c_int] * 6 + [vp, vp, vp, C.c_int, vp, vp, vp])
+    sig(L, "unet_conv3d_bwd_data", C.c_int, [C.c_int] * 6 + [vp, vp, vp, vp, vp])
+    sig(L, "unet_conv3d_bwd_weight", C.c_int, [C.c_int] * 6 + [vp, vp, vp, vp, vp])
+    sig(L, "unet_glue", C.c_int, [C.c_int] * 6 + [vp, vp, vp, vp, vp])
+    sig(L, "unet_head", C.c_int, [C.c_longlong] + [vp] * 9 + [vp])
     sig(L, "unet_num_params", C.c_int, [])
     sig(L, "unet_create", C.c_int, [C.c_ulonglong, vp, C.POINTER(vp)])
     sig(L, "unet_get_params", C.c_int, [vp, vp, C.c_int])
@@ -52,6 +56,7 @@ def declare(L, sig):
     sig(L, "warm_start_features", C.c_int, [C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, vp, vp, vp, dp, vp])
     sig(L, "warm_start_apply", C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, vp, C.c_double, vp, vp])
     sig(L, "gbsw_selftest_wait", C.c_int, [C.c_int, C.c_longlong])
+    sig(L, "gbsw_measure_l2_copy", C.c_int, [C.c_longlong, C.c_int, dp])
     sig(L, "gbsw_selftest_sor_division", C.c_int, [C.c_int, C.POINTER(C.c_ulonglong)])
     sig(L, "poisson_solve", C.c_int, [C.c_int, C.c_int, C.c_int, C.c_double, vp, vp, C.c_double, C.c_double,
                                       C.c_int, C.c_int, vp, ip, dp])

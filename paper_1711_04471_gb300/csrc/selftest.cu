@@ -5,6 +5,8 @@
 // GBSW_ERR_TIMEOUT and return, leaving the context usable.
 // gbsw_selftest_sor_division: the SOR sweep's division by the diagonal
 // (sor_div) against the IEEE division x / d for every finite FP32 x.
+// gbsw_measure_l2_copy: the copy bandwidth of buffers that stay in L2, the
+// ceiling of a kernel whose working set stays in L2 between passes.
 #include "common.cuh"
 #include "poisson.cuh"
 #include "tc.cuh"
@@ -58,7 +60,52 @@ __global__ void selftest_div_kernel(float d, float y, unsigned long long *out)
     if (bad_tiny) atomicAdd(&out[1], bad_tiny);
 }
 
+// passes x (dst = src) over n float4 words, grid-stride, in one launch.
+__global__ void __launch_bounds__(512) l2_copy_kernel(const float4 *__restrict__ src, float4 *__restrict__ dst,
+                                                      long long n, int passes)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (int p = 0; p < passes; ++p)
+        for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += stride) dst[q] = src[q];
+}
+
 }  // namespace
+
+extern "C" gbsw_status gbsw_measure_l2_copy(long long bytes, int passes, double *gbs)
+{
+    if (bytes < (1 << 20) || bytes % 16 || passes < 1 || passes > 10000 || !gbs) return GBSW_ERR_ARG;
+    float4 *buf = nullptr;
+    GBSW_CUDA_TRY(cudaMalloc((void **)&buf, 2 * (size_t)bytes));
+    const long long n = bytes / 16;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMemset(buf, 0, 2 * (size_t)bytes);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    double best = 0.0;
+    const int grid = 2 * gbsw::sm_count();  // 2 x 512 threads per SM, one wave
+    for (int rep = 0; rep < 6 && e == cudaSuccess; ++rep) {
+        cudaEventRecord(e0);
+        l2_copy_kernel<<<grid, 512>>>(buf, buf + n, n, passes);
+        cudaEventRecord(e1);
+        e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && rep > 0 && ms > 0.0f) {  // the first launch brings the buffers into L2
+            const double r = 2.0 * (double)bytes * passes / (ms * 1e-3) / 1e9;
+            if (r > best) best = r;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(buf);
+    if (e != cudaSuccess) {
+        gbsw::record_cuda_error(e, "gbsw_measure_l2_copy", __FILE__, __LINE__);
+        return GBSW_ERR_CUDA;
+    }
+    *gbs = best;
+    return GBSW_OK;
+}
 
 extern "C" gbsw_status gbsw_selftest_sor_division(int d, unsigned long long *counts)
 {

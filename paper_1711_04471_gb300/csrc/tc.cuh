@@ -87,9 +87,12 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
 __device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// Shared-memory matrix descriptor, no swizzle, K-major canonical layout:
+// Shared-memory matrix descriptor, no swizzle.  K-major canonical layout:
 // core matrices of 8 rows x 16 bytes; lbo = byte step between core matrices
-// along K, sbo = byte step between 8-row groups along M/N.
+// along K, sbo = byte step between 8-row groups along M/N.  MN-major
+// canonical layout: core matrices of 8 K-rows x 16 bytes (8 MN elements);
+// sbo = byte step between 8-element groups along M/N, lbo = byte step
+// between 8-row groups along K.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
 {
     uint64_t d = 0;
@@ -101,12 +104,14 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
 }
 
 // Instruction descriptor of kind::f16: BF16 A and B, FP32 accumulator,
-// both K-major, dense.
-__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N)
+// dense; both operands K-major unless mn_major (then both MN-major: the
+// transpose bits of A and B).
+__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N, bool mn_major = false)
 {
     return (1u << 4)                       // D format: F32
            | (1u << 7)                     // A format: BF16
            | (1u << 10)                    // B format: BF16
+           | (mn_major ? (1u << 15) | (1u << 16) : 0u)   // A, B MN-major
            | ((uint32_t)(N >> 3) << 17)    // N / 8
            | ((uint32_t)(M >> 4) << 24);   // M / 16
 }

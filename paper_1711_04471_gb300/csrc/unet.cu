@@ -1,16 +1,17 @@
 // The warm-start U-Net: parameters, activations, forward / backward
 // schedules, Adam training and the LES hook (see include/gbsw.h).
 //
-//   l1a 2->16 (CUDA cores), l1b 16->16                 -> s1   full resolution
+//   l1a 2->16 (input zero-padded to 16), l1b 16->16    -> s1   full resolution
 //   pool, l2a 16->32, l2b 32->32                        -> s2   1/2
 //   pool, l3a 32->64, l3b 64->32                                1/4
 //   upsample, cat [up, s2] (64), l2c 64->16                     1/2
 //   upsample, cat [up, s1] (32), l1c 32->16                     full
 //   head 1x1x1 16->1
-// Every 3x3x3 layer but l1a runs on the tcgen05 kernel (forward and the
-// backward-data pass with flipped weights); weight gradients run on CUDA
-// cores.  Concatenations are free: the producers write into channel-group
-// ranges of one buffer (u1 = [up(d2), s1], u2 = [up(b3), s2]).
+// Every 3x3x3 layer runs on the tcgen05 kernels: forward, backward-data
+// with flipped weights and weight gradients (l1a's two input channels are
+// zero-padded to 16 in a BF16 copy of the input).  Concatenations are
+// free: the producers write into channel-group ranges of one buffer
+// (u1 = [up(d2), s1], u2 = [up(b3), s2]).
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -46,11 +47,12 @@ struct Acts {
     ConvGeom g[3];             // levels 1..3
     long long nvox;            // full-resolution voxels
     float *xin = nullptr, *out = nullptr;
+    bf16 *x16 = nullptr;       // xin as C8-blocked BF16, channels 2..15 zero (l1a's padded input)
     double *ws = nullptr;      // warm start: block means r_c, p_c (nvox each) and the scale
     bf16 *a1a, *u1, *p1, *a2a, *u2, *p2, *a3a, *b3, *d2, *d1;
     bf16 *g_d1 = nullptr, *g_u1, *g_d2, *g_u2, *g_b3, *g_a3a, *g_p2, *g_s2, *g_a2a, *g_p1, *g_s1, *g_a1a;
-    CUtensorMap m_fwd[NLAYERS];  // input map of each layer's forward conv (l1a unused)
-    CUtensorMap m_bwd[NLAYERS];  // input (gz) map of each layer's backward-data conv
+    CUtensorMap m_fwd[NLAYERS];  // input map of each layer's forward conv (and of its weight gradient)
+    CUtensorMap m_bwd[NLAYERS];  // map of each layer's gz: input of its backward-data conv and of its weight gradient
     std::vector<void *> allocs;
     bool train = false;
 };
@@ -112,6 +114,12 @@ gbsw_status make_acts(int N, int D, int H, int W, bool train, Acts **out)
     if (st == GBSW_OK) st = alloc(a, &a->xin, (size_t)v1 * 2);
     if (st == GBSW_OK) st = alloc(a, &a->out, (size_t)v1);
     if (st == GBSW_OK && N == 1) st = alloc(a, &a->ws, (size_t)(2 * v1 + 1));
+    B(&a->x16, v1, 16);
+    // the padding channels stay zero for the life of the buffer; finish
+    // the fill before any stream (the caller's or the LES's) uses it
+    if (st == GBSW_OK && (cudaMemset(a->x16, 0, (size_t)v1 * 16 * sizeof(bf16)) != cudaSuccess ||
+                          cudaDeviceSynchronize() != cudaSuccess))
+        st = GBSW_ERR_CUDA;
     B(&a->a1a, v1, 16);
     B(&a->u1, v1, 32);
     B(&a->p1, v2, 16);
@@ -145,15 +153,15 @@ gbsw_status make_acts(int N, int D, int H, int W, bool train, Acts **out)
         const ConvGeom *g;
         int cg;
     };
-    const M fwd[] = {{L1B, a->a1a, &g1, 2}, {L2A, a->p1, &g2, 2}, {L2B, a->a2a, &g2, 4}, {L3A, a->p2, &g3, 4},
-                     {L3B, a->a3a, &g3, 8}, {L2C, a->u2, &g2, 8}, {L1C, a->u1, &g1, 4}};
+    const M fwd[] = {{L1A, a->x16, &g1, 2}, {L1B, a->a1a, &g1, 2}, {L2A, a->p1, &g2, 2}, {L2B, a->a2a, &g2, 4},
+                     {L3A, a->p2, &g3, 4},  {L3B, a->a3a, &g3, 8}, {L2C, a->u2, &g2, 8}, {L1C, a->u1, &g1, 4}};
     for (const M &m : fwd)
         if (st == GBSW_OK) st = conv_tensor_map(m.p, *m.g, m.cg, &a->m_fwd[m.layer]);
     if (train) {
-        // backward-data inputs: the gz of each layer (Cout channels)
-        const M bwd[] = {{L1B, a->g_s1, &g1, 2}, {L2A, a->g_a2a, &g2, 4}, {L2B, a->g_s2, &g2, 4},
-                         {L3A, a->g_a3a, &g3, 8}, {L3B, a->g_b3, &g3, 4}, {L2C, a->g_d2, &g2, 2},
-                         {L1C, a->g_d1, &g1, 2}};
+        // the gz of each layer (Cout channels): backward-data and weight-gradient input
+        const M bwd[] = {{L1A, a->g_a1a, &g1, 2}, {L1B, a->g_s1, &g1, 2}, {L2A, a->g_a2a, &g2, 4},
+                         {L2B, a->g_s2, &g2, 4},  {L3A, a->g_a3a, &g3, 8}, {L3B, a->g_b3, &g3, 4},
+                         {L2C, a->g_d2, &g2, 2},  {L1C, a->g_d1, &g1, 2}};
         for (const M &m : bwd)
             if (st == GBSW_OK) st = conv_tensor_map(m.p, *m.g, m.cg, &a->m_bwd[m.layer]);
     }
@@ -186,9 +194,16 @@ gbsw_status get_acts(gbsw_unet *u, int N, int D, int H, int W, bool train, Acts 
     return GBSW_OK;
 }
 
+#define TRY(x)                          \
+    do {                                \
+        gbsw_status _s = (x);           \
+        if (_s != GBSW_OK) return _s;   \
+    } while (0)
+
 gbsw_status repack(gbsw_unet *u, cudaStream_t s)
 {
     if (!u->packs_dirty) return GBSW_OK;
+    TRY(pack_weights_padded(u->params + u->w_off[L1A], LAYERS[L1A].cin, 16, LAYERS[L1A].cout, 0, u->pack_fwd[L1A], s));
     for (int l = 1; l < NLAYERS; ++l) {
         gbsw_status st = pack_weights(u->params + u->w_off[l], LAYERS[l].cin, LAYERS[l].cout, 0, u->pack_fwd[l], s);
         if (st == GBSW_OK)
@@ -222,11 +237,6 @@ gbsw_status conv(gbsw_unet *u, int cin, int cout, const CUtensorMap &map, const 
     return launch_conv(cin, cout, c, s);
 }
 
-#define TRY(x)                          \
-    do {                                \
-        gbsw_status _s = (x);           \
-        if (_s != GBSW_OK) return _s;   \
-    } while (0)
 
 // Forward pass on a->xin; writes a->out.
 gbsw_status forward(gbsw_unet *u, Acts *a, cudaStream_t s)
@@ -236,7 +246,8 @@ gbsw_status forward(gbsw_unet *u, Acts *a, cudaStream_t s)
     float *P = u->params;
     auto W = [&](int l) { return u->pack_fwd[l]; };
     auto Bv = [&](int l) { return P + u->b_off[l]; };
-    TRY(launch_conv_in2(a->xin, P + u->w_off[L1A], Bv(L1A), g1, a->a1a, 2, 0, s));
+    TRY(to_blocked(a->xin, g1.NZ, g1.H, g1.W, 2, a->x16, 2, 0, s));
+    TRY(conv(u, 16, 16, a->m_fwd[L1A], W(L1A), Bv(L1A), g1, a->a1a, 2, 0, EPI_BIAS_RELU, nullptr, 0, 0, s));
     TRY(conv(u, 16, 16, a->m_fwd[L1B], W(L1B), Bv(L1B), g1, a->u1, 4, 2, EPI_BIAS_RELU, nullptr, 0, 0, s));
     TRY(launch_pool(a->u1, 4, 2, g1.NZ, g1.H, g1.W, 16, a->p1, 2, 0, s));
     TRY(conv(u, 16, 32, a->m_fwd[L2A], W(L2A), Bv(L2A), g2, a->a2a, 4, 0, EPI_BIAS_RELU, nullptr, 0, 0, s));
@@ -252,6 +263,23 @@ gbsw_status forward(gbsw_unet *u, Acts *a, cudaStream_t s)
     return GBSW_OK;
 }
 
+// Weight and bias gradients of layer l from its input (m_fwd[l]) and its
+// gz (m_bwd[l], the C8-blocked tensor gz with cout / 8 channel groups).
+gbsw_status wgrad(gbsw_unet *u, Acts *a, int l, const ConvGeom &g, const bf16 *gz, cudaStream_t s)
+{
+    WgradCall c{};
+    c.xmap = a->m_fwd[l];
+    c.gmap = a->m_bwd[l];
+    c.geom = g;
+    c.dw = u->grads + u->w_off[l];
+    c.cin_store = LAYERS[l].cin;
+    c.status = u->status;
+    const int cin = l == L1A ? 16 : LAYERS[l].cin;
+    TRY(launch_wgrad_tc(cin, LAYERS[l].cout, c, s));
+    const long long nvox = (long long)g.NZ * g.H * g.W;
+    return launch_bias_grad(gz, LAYERS[l].cout / 8, 0, nvox, g.H, g.W, LAYERS[l].cout, u->grads + u->b_off[l], s);
+}
+
 // Backward pass of MSE(out, target) after forward(); accumulates into
 // u->grads (zeroed here) and adds the loss to *u->loss.
 gbsw_status backward(gbsw_unet *u, Acts *a, const float *target, cudaStream_t s)
@@ -259,34 +287,32 @@ gbsw_status backward(gbsw_unet *u, Acts *a, const float *target, cudaStream_t s)
     const ConvGeom &g1 = a->g[0], &g2 = a->g[1], &g3 = a->g[2];
     float *G = u->grads;
     auto WB = [&](int l) { return u->pack_bwd[l]; };
-    auto GW = [&](int l) { return G + u->w_off[l]; };
-    auto GB = [&](int l) { return G + u->b_off[l]; };
     GBSW_CUDA_TRY(cudaMemsetAsync(G, 0, (size_t)u->nparams * sizeof(float), s));
     TRY(launch_head_bwd(a->d1, 2, 0, a->nvox, g1.H, g1.W, a->out, target, u->params + u->hw_off, G + u->hw_off,
                         G + u->hb_off, a->g_d1, u->loss, s));
     // l1c: input u1 = [up(d2), s1]
-    TRY(launch_wgrad(32, 16, a->u1, 4, 0, a->g_d1, 2, 0, g1, GW(L1C), GB(L1C), s));
+    TRY(wgrad(u, a, L1C, g1, a->g_d1, s));
     TRY(conv(u, 16, 32, a->m_bwd[L1C], WB(L1C), nullptr, g1, a->g_u1, 4, 0, EPI_MASK, a->u1, 4, 0, s));
     TRY(launch_upsample_bwd(a->g_u1, 4, 0, g2.NZ, g2.H, g2.W, 16, a->g_d2, 2, 0, s));
     // l2c: input u2 = [up(b3), s2]
-    TRY(launch_wgrad(64, 16, a->u2, 8, 0, a->g_d2, 2, 0, g2, GW(L2C), GB(L2C), s));
+    TRY(wgrad(u, a, L2C, g2, a->g_d2, s));
     TRY(conv(u, 16, 64, a->m_bwd[L2C], WB(L2C), nullptr, g2, a->g_u2, 8, 0, EPI_MASK, a->u2, 8, 0, s));
     TRY(launch_upsample_bwd(a->g_u2, 8, 0, g3.NZ, g3.H, g3.W, 32, a->g_b3, 4, 0, s));
     // l3b, l3a
-    TRY(launch_wgrad(64, 32, a->a3a, 8, 0, a->g_b3, 4, 0, g3, GW(L3B), GB(L3B), s));
+    TRY(wgrad(u, a, L3B, g3, a->g_b3, s));
     TRY(conv(u, 32, 64, a->m_bwd[L3B], WB(L3B), nullptr, g3, a->g_a3a, 8, 0, EPI_MASK, a->a3a, 8, 0, s));
-    TRY(launch_wgrad(32, 64, a->p2, 4, 0, a->g_a3a, 8, 0, g3, GW(L3A), GB(L3A), s));
+    TRY(wgrad(u, a, L3A, g3, a->g_a3a, s));
     TRY(conv(u, 64, 32, a->m_bwd[L3A], WB(L3A), nullptr, g3, a->g_p2, 4, 0, EPI_RAW, nullptr, 0, 0, s));
     // s2 receives the concat gradient and the pooled path
     TRY(launch_pool_bwd_add_mask(a->g_u2, 8, 4, a->g_p2, 4, 0, a->u2, 8, 4, g2.NZ, g2.H, g2.W, 32, a->g_s2, 4, 0, s));
-    TRY(launch_wgrad(32, 32, a->a2a, 4, 0, a->g_s2, 4, 0, g2, GW(L2B), GB(L2B), s));
+    TRY(wgrad(u, a, L2B, g2, a->g_s2, s));
     TRY(conv(u, 32, 32, a->m_bwd[L2B], WB(L2B), nullptr, g2, a->g_a2a, 4, 0, EPI_MASK, a->a2a, 4, 0, s));
-    TRY(launch_wgrad(16, 32, a->p1, 2, 0, a->g_a2a, 4, 0, g2, GW(L2A), GB(L2A), s));
+    TRY(wgrad(u, a, L2A, g2, a->g_a2a, s));
     TRY(conv(u, 32, 16, a->m_bwd[L2A], WB(L2A), nullptr, g2, a->g_p1, 2, 0, EPI_RAW, nullptr, 0, 0, s));
     TRY(launch_pool_bwd_add_mask(a->g_u1, 4, 2, a->g_p1, 2, 0, a->u1, 4, 2, g1.NZ, g1.H, g1.W, 16, a->g_s1, 2, 0, s));
-    TRY(launch_wgrad(16, 16, a->a1a, 2, 0, a->g_s1, 2, 0, g1, GW(L1B), GB(L1B), s));
+    TRY(wgrad(u, a, L1B, g1, a->g_s1, s));
     TRY(conv(u, 16, 16, a->m_bwd[L1B], WB(L1B), nullptr, g1, a->g_a1a, 2, 0, EPI_MASK, a->a1a, 2, 0, s));
-    TRY(launch_wgrad_in2(a->xin, a->g_a1a, 2, 0, g1, GW(L1A), GB(L1A), s));
+    TRY(wgrad(u, a, L1A, g1, a->g_a1a, s));
     return GBSW_OK;
 }
 
@@ -373,6 +399,8 @@ gbsw_status unet_create(unsigned long long seed, void *stream, gbsw_unet **out)
         cudaMalloc((void **)&u->status, sizeof(int)) != cudaSuccess ||
         cudaMalloc((void **)&u->loss, sizeof(double)) != cudaSuccess)
         return fail(GBSW_ERR_OOM);
+    if (cudaMalloc((void **)&u->pack_fwd[L1A], (size_t)27 * 16 * 16 * sizeof(bf16)) != cudaSuccess)
+        return fail(GBSW_ERR_OOM);  // l1a: input channels padded to 16; no backward-data pack
     for (int l = 1; l < NLAYERS; ++l) {
         const size_t n = (size_t)27 * LAYERS[l].cin * LAYERS[l].cout * sizeof(bf16);
         if (cudaMalloc((void **)&u->pack_fwd[l], n) != cudaSuccess || cudaMalloc((void **)&u->pack_bwd[l], n) != cudaSuccess)

@@ -4,6 +4,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "unet_conv.cuh"
@@ -171,10 +172,189 @@ conv3d_tc_kernel(const __grid_constant__ CUtensorMap xmap, const __nv_bfloat16 *
     if (warp == 0) tc::tmem_dealloc(tmem, S::TMEM_COLS);
 }
 
+// ------------------------------------------------------------ weight grads
+// Shared memory of wgrad_tc_kernel: a ring of stages, each holding the
+// shifted x tiles of one group of TPG = 128 / CIN taps (the A operand, 128
+// rows (tap, ci) of 2048-byte channel-group slabs, 32 KB) and the gz tile
+// (B, COUT / 8 slabs).
+template <int CIN, int COUT>
+struct WgradSmem {
+    static constexpr int TPG = 128 / CIN;                     // taps per MMA group
+    static constexpr int NGROUPS = (27 + TPG - 1) / TPG;
+    static constexpr int A_BYTES = 128 * 128 * 2;             // 16 slabs of 128 voxels x 16 B
+    static constexpr int B_BYTES = COUT * 128 * 2;
+    static constexpr int STAGE = A_BYTES + B_BYTES;           // a multiple of 2048
+    static constexpr int STAGES = 4;
+    static constexpr int BAR_OFF = STAGES * STAGE;
+    static constexpr int BYTES = BAR_OFF + 128 + 1024;
+    static constexpr int COLS_USED = NGROUPS * COUT;
+    static constexpr int TMEM_COLS = COLS_USED <= 32 ? 32 : COLS_USED <= 64 ? 64 : COLS_USED <= 128 ? 128
+                                   : COLS_USED <= 256 ? 256 : 512;
+};
+
+// dW[tap][co][ci] += sum over the voxels of tiles [t_begin, t_end) of
+// gz[v][co] x[v + off(tap)][ci] (zero outside the sample), one CTA per
+// chunk of tiles.  Per tile and tap group: thread 0 loads the group's
+// shifted x tiles (the forward conv's TMA boxes; a plane whose tap leaves
+// its sample, or past the last plane, is loaded from z = -1, all zero
+// fill) and the gz tile into a stage; thread 32 issues 8 MMAs (M = 128
+// rows (tap, ci), N = COUT, K = 16 voxels, both operands MN-major) into
+// the group's TMEM columns; at the end the four warps add their 128 lanes
+// (rows) of every group to dw with atomics.
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(CONV_THREADS)
+wgrad_tc_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap gmap, ConvGeom g,
+                int tiles_per_cta, float *__restrict__ dw, int cin_store, int *status)
+{
+    using S = WgradSmem<CIN, COUT>;
+    static_assert(CIN % 16 == 0 && 128 % CIN == 0 && COUT % 16 == 0 && S::COLS_USED <= 512, "wgrad shape");
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t *full = (uint64_t *)(smem + S::BAR_OFF);
+    uint64_t *empty = full + S::STAGES;
+    uint64_t *done = empty + S::STAGES;
+    uint32_t *tmem_slot = (uint32_t *)(done + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ntiles = g.tiles_x * g.tiles_y * g.tiles_z;
+    const int t_begin = blockIdx.x * tiles_per_cta;
+    const int t_end = min(ntiles, t_begin + tiles_per_cta);
+    const bool multi = g.box_z > 1;
+    const int plane_bytes = g.box_x * g.box_y * 16;
+
+    // rows of a partial last group read stale stage bytes: start them as zeros
+    for (int q = threadIdx.x; q < S::STAGES * S::STAGE / 16; q += CONV_THREADS)
+        reinterpret_cast<uint4 *>(smem)[q] = make_uint4(0, 0, 0, 0);
+    if (warp == 0) {
+        tc::tmem_alloc(tmem_slot, S::TMEM_COLS);
+        tc::tmem_relinquish();
+    }
+    if (threadIdx.x == 32) {
+        for (int s = 0; s < S::STAGES; ++s) {
+            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&empty[s], 1);
+        }
+        tc::mbar_init(done, 1);
+        tc::fence_mbar_init();
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the zeros before any TMA / MMA access
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+
+    if (threadIdx.x == 0) {
+        // producer
+        int it = 0;
+        bool ok = true;
+        for (int t = t_begin; t < t_end && ok; ++t) {
+            int tt = t;
+            const int x0 = (tt % g.tiles_x) * g.box_x;
+            tt /= g.tiles_x;
+            const int y0 = (tt % g.tiles_y) * g.box_y;
+            const int z0 = (tt / g.tiles_y) * g.box_z;
+            for (int gi = 0; gi < S::NGROUPS; ++gi, ++it) {
+                const int s = it % S::STAGES;
+                if (it >= S::STAGES && !tc::mbar_wait(&empty[s], ((it / S::STAGES) - 1) & 1)) {
+                    set_status(status, DEV_TIMEOUT);
+                    ok = false;
+                    break;
+                }
+                const int tap0 = gi * S::TPG;
+                const int ntap = min(S::TPG, 27 - tap0);
+                uint8_t *a = smem + s * S::STAGE;
+                uint8_t *b = a + S::A_BYTES;
+                tc::mbar_arrive_expect_tx(&full[s], ntap * CIN * 256 + COUT * 256);
+                for (int q = 0; q < ntap; ++q) {
+                    const int tap = tap0 + q;
+                    const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+                    uint8_t *dst = a + q * (CIN / 8) * 2048;
+                    if (!multi) {
+                        const int z = z0 % g.D;
+                        const int zsrc = (z + dz >= 0 && z + dz < g.D) ? z0 + dz : -1;
+                        tc::tma_load_5d(dst, &xmap, &full[s], 0, x0 + dx, y0 + dy, 0, zsrc);
+                    } else {
+                        for (int zz = 0; zz < g.box_z; ++zz) {
+                            const int zn = z0 + zz, zi = zn % g.D;
+                            const int zsrc = (zn < g.NZ && zi + dz >= 0 && zi + dz < g.D) ? zn + dz : -1;
+                            for (int cg = 0; cg < CIN / 8; ++cg)
+                                tc::tma_load_5d(dst + cg * 2048 + zz * plane_bytes, &xmap, &full[s], 0, x0 + dx,
+                                                y0 + dy, cg, zsrc);
+                        }
+                    }
+                }
+                if (!multi) {
+                    tc::tma_load_5d(b, &gmap, &full[s], 0, x0, y0, 0, z0);
+                } else {
+                    for (int zz = 0; zz < g.box_z; ++zz) {
+                        const int zn = z0 + zz;
+                        for (int cg = 0; cg < COUT / 8; ++cg)
+                            tc::tma_load_5d(b + cg * 2048 + zz * plane_bytes, &gmap, &full[s], 0, x0, y0, cg,
+                                            zn < g.NZ ? zn : -1);
+                    }
+                }
+            }
+        }
+    } else if (threadIdx.x == 32) {
+        // MMA issuer
+        constexpr uint32_t idesc = tc::idesc_bf16_f32(128, COUT, true);
+        int it = 0;
+        bool ok = true;
+        for (int t = t_begin; t < t_end && ok; ++t) {
+            for (int gi = 0; gi < S::NGROUPS; ++gi, ++it) {
+                const int s = it % S::STAGES;
+                if (!tc::mbar_wait(&full[s], (it / S::STAGES) & 1)) {
+                    set_status(status, DEV_TIMEOUT);
+                    ok = false;
+                    break;
+                }
+                tc::fence_after_sync();
+                const uint32_t a = tc::smem_u32(smem + s * S::STAGE);
+                const uint32_t b = a + S::A_BYTES;
+#pragma unroll
+                for (int kc = 0; kc < 8; ++kc) {
+                    // K = 16 voxels per MMA: the start moves by 16 voxels x 16 B
+                    const uint64_t ad = tc::smem_desc(a + kc * 256, 128, 2048);
+                    const uint64_t bd = tc::smem_desc(b + kc * 256, 128, 2048);
+                    tc::umma_bf16(tmem + gi * COUT, ad, bd, idesc, (t > t_begin || kc > 0) ? 1u : 0u);
+                }
+                tc::umma_commit(&empty[s]);
+            }
+        }
+        tc::umma_commit(done);
+    }
+
+    // epilogue: lane = row (tap, ci) of a group, 8 output channels per load
+    __syncwarp();
+    const bool ready = t_end > t_begin && tc::mbar_wait(done, 0);
+    if (!ready && t_end > t_begin && lane == 0) set_status(status, DEV_TIMEOUT);
+    tc::fence_after_sync();
+    const int row = warp * 32 + lane;
+    const int ci = row % CIN;
+#pragma unroll 1
+    for (int gi = 0; gi < S::NGROUPS; ++gi) {
+        const int tap = gi * S::TPG + row / CIN;
+#pragma unroll
+        for (int cb = 0; cb < COUT / 8; ++cb) {
+            float v[8];
+            tc::tmem_ld8(tmem + ((uint32_t)(warp * 32) << 16) + gi * COUT + cb * 8, v);
+            if (!ready || tap >= 27 || ci >= cin_store) continue;
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                atomicAdd(&dw[((size_t)tap * COUT + cb * 8 + q) * cin_store + ci], v[q]);
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, S::TMEM_COLS);
+}
+
 // pack[tap][ci/8][co][ci%8] = w[tap][co][ci]   (forward), or with
 // flip = 1 the weights of the backward-data convolution:
-// pack[tap][co/8][ci][co%8] = w[26 - tap][co][ci].
-__global__ void conv_pack_kernel(const float *__restrict__ w, int cin, int cout, int flip,
+// pack[tap][co/8][ci][co%8] = w[26 - tap][co][ci].  The source holds
+// cin_src <= cin input channels per (tap, co); the forward pack's channels
+// ci >= cin_src are zero (a zero-padded input).
+__global__ void conv_pack_kernel(const float *__restrict__ w, int cin_src, int cin, int cout, int flip,
                                  __nv_bfloat16 *__restrict__ pack)
 {
     const int n = 27 * cin * cout;
@@ -183,7 +363,7 @@ __global__ void conv_pack_kernel(const float *__restrict__ w, int cin, int cout,
     const int tap = q / (cin * cout);
     const int r = q % (cin * cout);
     const int co = r / cin, ci = r % cin;
-    const float v = w[q];
+    const float v = ci < cin_src ? w[((size_t)tap * cout + co) * cin_src + ci] : 0.0f;
     size_t dst;
     if (!flip) {
         dst = (((size_t)tap * (cin / 8) + ci / 8) * cout + co) * 8 + ci % 8;
@@ -261,6 +441,27 @@ gbsw_status launch_conv_t(const ConvCall &c, cudaStream_t s)
     return GBSW_OK;
 }
 
+template <int CIN, int COUT>
+gbsw_status launch_wgrad_t(const WgradCall &c, cudaStream_t s)
+{
+    using S = WgradSmem<CIN, COUT>;
+    static bool configured = false;
+    if (!configured) {
+        GBSW_CUDA_TRY(cudaFuncSetAttribute(wgrad_tc_kernel<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           S::BYTES));
+        configured = true;
+    }
+    const int ntiles = c.geom.tiles_z * c.geom.tiles_y * c.geom.tiles_x;
+    // one CTA per SM at most (the ring takes most of the shared memory); a
+    // few tiles per CTA amortise the epilogue's atomics
+    const int ctas = std::max(1, std::min(ntiles, sm_count()));
+    const int per = ceil_div(ntiles, ctas);
+    wgrad_tc_kernel<CIN, COUT><<<ceil_div(ntiles, per), CONV_THREADS, S::BYTES, s>>>(c.xmap, c.gmap, c.geom, per,
+                                                                                     c.dw, c.cin_store, c.status);
+    GBSW_LAUNCH_CHECK();
+    return GBSW_OK;
+}
+
 }  // namespace
 
 // Geometry of a conv over a C8-blocked tensor of NZ planes of H x W voxels.
@@ -327,10 +528,32 @@ gbsw_status launch_conv(int cin, int cout, const ConvCall &c, cudaStream_t s)
     return GBSW_ERR_ARG;
 }
 
+gbsw_status launch_wgrad_tc(int cin, int cout, const WgradCall &c, cudaStream_t s)
+{
+#define WG_CASE(A, B) \
+    if (cin == A && cout == B) return launch_wgrad_t<A, B>(c, s);
+    WG_CASE(16, 16)
+    WG_CASE(16, 32)
+    WG_CASE(32, 16)
+    WG_CASE(32, 32)
+    WG_CASE(32, 64)
+    WG_CASE(64, 16)
+    WG_CASE(64, 32)
+#undef WG_CASE
+    return GBSW_ERR_ARG;
+}
+
 gbsw_status pack_weights(const float *w, int cin, int cout, int flip, __nv_bfloat16 *pack, cudaStream_t s)
 {
+    return pack_weights_padded(w, cin, cin, cout, flip, pack, s);
+}
+
+gbsw_status pack_weights_padded(const float *w, int cin_src, int cin, int cout, int flip, __nv_bfloat16 *pack,
+                                cudaStream_t s)
+{
+    if (cin_src < 1 || cin_src > cin || (flip && cin_src != cin)) return GBSW_ERR_ARG;
     const int n = 27 * cin * cout;
-    conv_pack_kernel<<<ceil_div(n, 256), 256, 0, s>>>(w, cin, cout, flip, pack);
+    conv_pack_kernel<<<ceil_div(n, 256), 256, 0, s>>>(w, cin_src, cin, cout, flip, pack);
     GBSW_LAUNCH_CHECK();
     return GBSW_OK;
 }
@@ -354,54 +577,3 @@ gbsw_status from_blocked(const __nv_bfloat16 *src, int NZ, int H, int W, int C, 
 }
 
 }  // namespace gbsw
-
-using namespace gbsw;
-
-extern "C" gbsw_status unet_conv3d(int nsamples, int D, int H, int W, int cin, int cout, const float *x,
-                                   const float *w, const float *bias, int epilogue, const float *mask, float *y,
-                                   void *stream)
-{
-    if (!x || !w || !y || nsamples < 1 || cin % 16 || cout % 16 || epilogue < 0 || epilogue > 2) return GBSW_ERR_ARG;
-    if (epilogue == EPI_BIAS_RELU && !bias) return GBSW_ERR_ARG;
-    if (epilogue == EPI_MASK && !mask) return GBSW_ERR_ARG;
-    cudaStream_t s = (cudaStream_t)stream;
-    ConvGeom g;
-    gbsw_status st = conv_geometry(nsamples * D, D, H, W, &g);
-    if (st != GBSW_OK) return st;
-    const size_t nv = (size_t)nsamples * D * H * W;
-    __nv_bfloat16 *xb = nullptr, *wp = nullptr, *mb = nullptr;
-    int *status = nullptr;
-    int hstatus = 0;
-    do {
-        GBSW_CUDA_TRY(cudaMalloc((void **)&xb, nv * cin * sizeof(__nv_bfloat16)));
-        GBSW_CUDA_TRY(cudaMalloc((void **)&wp, (size_t)27 * cin * cout * sizeof(__nv_bfloat16)));
-        GBSW_CUDA_TRY(cudaMalloc((void **)&status, sizeof(int)));
-        GBSW_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), s));
-        if (epilogue == EPI_MASK) {
-            GBSW_CUDA_TRY(cudaMalloc((void **)&mb, nv * cout * sizeof(__nv_bfloat16)));
-            if ((st = to_blocked(mask, g.NZ, H, W, cout, mb, cout / 8, 0, s)) != GBSW_OK) break;
-        }
-        if ((st = to_blocked(x, g.NZ, H, W, cin, xb, cin / 8, 0, s)) != GBSW_OK) break;
-        if ((st = pack_weights(w, cin, cout, 0, wp, s)) != GBSW_OK) break;
-        ConvCall c{};
-        if ((st = conv_tensor_map(xb, g, cin / 8, &c.xmap)) != GBSW_OK) break;
-        g.mask_cg_total = cout / 8;
-        c.geom = g;
-        c.wpack = wp;
-        c.bias = bias;
-        c.y = nullptr;
-        c.y_f32 = y;
-        c.mask = mb;
-        c.epi = epilogue;
-        c.status = status;
-        if ((st = launch_conv(cin, cout, c, s)) != GBSW_OK) break;
-        GBSW_CUDA_TRY(cudaMemcpyAsync(&hstatus, status, sizeof(int), cudaMemcpyDeviceToHost, s));
-        GBSW_CUDA_TRY(cudaStreamSynchronize(s));
-    } while (0);
-    cudaFree(xb);
-    cudaFree(wp);
-    cudaFree(mb);
-    cudaFree(status);
-    if (st != GBSW_OK) return st;
-    return dev_status_to_gbsw(hstatus);
-}

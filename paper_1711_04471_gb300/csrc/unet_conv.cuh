@@ -28,6 +28,16 @@
 // per tap and commits each stage back to the producer, and all four warps
 // read the accumulator (warp w owns TMEM lanes 32w..32w+31 = voxels) for
 // the epilogue.
+//
+// Weight gradients (wgrad_tc_kernel) contract over voxels instead:
+// dW[tap][co][ci] = sum_v gz[v][co] x[v + off(tap)][ci].  The same
+// C8-blocked tiles, read with K = voxels, are MN-major operands (the 8
+// channels of a voxel contiguous, consecutive voxels 16 bytes apart): core
+// matrix = 8 voxels x 8 channels = 128 B, K step (next 8 voxels) 128 B, MN
+// step (next 8 channels) 2048 B.  128 / Cin taps' shifted x tiles, stacked,
+// form the 128 rows (tap, ci) of the A operand; the gz tile is B (N = Cout
+// rows); every tap's accumulator stays in TMEM while the CTA walks its
+// voxel tiles.
 #pragma once
 
 #include "common.cuh"
@@ -43,6 +53,19 @@ struct ConvGeom {
     int tiles_x, tiles_y, tiles_z;
     int out_cg_total, out_cg0;    // output tensor channel groups and offset
     int mask_cg_total, mask_cg0;  // mask tensor (EPI_MASK)
+};
+
+// Arguments of one weight-gradient launch (dw accumulates with atomics:
+// zero it first).  xmap: the layer input (Cin channels), gmap: the
+// gradient of the layer output before the bias (Cout channels), both
+// C8-blocked with the forward conv's boxes; only input channels
+// ci < cin_store are written, at dw[(tap * Cout + co) * cin_store + ci].
+struct WgradCall {
+    CUtensorMap xmap, gmap;
+    ConvGeom geom;
+    float *dw;
+    int cin_store;
+    int *status;
 };
 
 enum ConvEpilogue : int {

@@ -1,6 +1,5 @@
-// U-Net glue kernels: the first (2-channel) convolution on CUDA cores,
-// pooling / upsampling in the C8-blocked layout, the 1x1 head with the MSE
-// loss, weight gradients and Adam.
+// U-Net glue kernels: bias gradients, pooling / upsampling in the
+// C8-blocked layout, the 1x1 head with the MSE loss, and Adam.
 #include <algorithm>
 
 #include "unet_ops.cuh"
@@ -12,193 +11,39 @@ __device__ __forceinline__ size_t bidx(int zn, int cg_total, int cg, int H, int 
     return ((((size_t)zn * cg_total + cg) * H + y) * W + x) * 8;
 }
 
-// ---------------------------------------------------------------- layer l1a
-// y = relu(conv(x) + b) with x dense FP32 (zn, y, x, 2), 16 outputs into a
-// C8-blocked tensor.  One thread per voxel; weights in shared memory.
-__global__ void conv_in2_kernel(const float *__restrict__ x, const float *__restrict__ w, const float *__restrict__ b,
-                                int NZ, int D, int H, int W, __nv_bfloat16 *__restrict__ y, int cg_total, int cg0)
+// ------------------------------------------------------------ bias grads
+// db[co] += sum_v g[v, co] over a C8-blocked g (C channels at groups
+// cg0 .. cg0 + C/8 - 1).  Thread t takes channel group t % (C/8) of the
+// voxels t / (C/8), + 256 / (C/8), ...; the block then sums its threads'
+// partials in a fixed order and adds one value per channel to db.
+// Launch: block 256.
+__global__ void __launch_bounds__(256)
+bias_grad_kernel(const __nv_bfloat16 *__restrict__ g, int g_cg_total, int g_cg0, long long nvox, int H, int W, int C,
+                 float *__restrict__ db)
 {
-    __shared__ float sw[27 * 16 * 2];
-    __shared__ float sb[16];
-    for (int q = threadIdx.x; q < 27 * 32; q += blockDim.x) sw[q] = w[q];
-    if (threadIdx.x < 16) sb[threadIdx.x] = b[threadIdx.x];
-    __syncthreads();
-    const long long n = (long long)NZ * H * W;
-    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= n) return;
-    const int xx = (int)(v % W);
-    const int yy = (int)((v / W) % H);
-    const int zn = (int)(v / ((long long)W * H));
-    const int z = zn % D;
-    float acc[16];
-#pragma unroll
-    for (int co = 0; co < 16; ++co) acc[co] = sb[co];
-    for (int tap = 0; tap < 27; ++tap) {
-        const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-        if (z + dz < 0 || z + dz >= D || yy + dy < 0 || yy + dy >= H || xx + dx < 0 || xx + dx >= W) continue;
-        const float2 in = *reinterpret_cast<const float2 *>(x + ((((size_t)(zn + dz) * H) + yy + dy) * W + xx + dx) * 2);
-#pragma unroll
-        for (int co = 0; co < 16; ++co) acc[co] += sw[(tap * 16 + co) * 2] * in.x + sw[(tap * 16 + co) * 2 + 1] * in.y;
-    }
-#pragma unroll
-    for (int g = 0; g < 2; ++g) {
-        uint4 pk;
-        __nv_bfloat162 *p2 = reinterpret_cast<__nv_bfloat162 *>(&pk);
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-            p2[q] = __floats2bfloat162_rn(fmaxf(acc[g * 8 + 2 * q], 0.0f), fmaxf(acc[g * 8 + 2 * q + 1], 0.0f));
-        *reinterpret_cast<uint4 *>(y + bidx(zn, cg_total, cg0 + g, H, W, yy, xx)) = pk;
-    }
-}
-
-// dW of l1a: dw[tap][co][ci] += sum_v g[v, co] x[v + off(tap), ci], db[co] += sum_v g[v, co].
-// grid (27, chunks), block 256; g is C8-blocked (16 ch), x dense FP32 (2 ch).
-__global__ void wgrad_in2_kernel(const float *__restrict__ x, const __nv_bfloat16 *__restrict__ g, int g_cg_total,
-                                 int g_cg0, int NZ, int D, int H, int W, float *__restrict__ dw, float *__restrict__ db)
-{
-    const int tap = blockIdx.x;
-    const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-    float acc[32];
-    float accb[16];
-#pragma unroll
-    for (int q = 0; q < 32; ++q) acc[q] = 0.0f;
-#pragma unroll
-    for (int q = 0; q < 16; ++q) accb[q] = 0.0f;
-    const long long n = (long long)NZ * H * W;
-    for (long long v = (long long)blockIdx.y * blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.y * blockDim.x) {
+    __shared__ float red[256][9];
+    const int ng = C / 8;                 // 2, 4 or 8: divides 256
+    const int lanes = 256 / ng;           // threads per channel group
+    const int cb = threadIdx.x % ng, r = threadIdx.x / ng;
+    float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (long long v = (long long)blockIdx.x * lanes + r; v < nvox; v += (long long)gridDim.x * lanes) {
         const int xx = (int)(v % W);
         const int yy = (int)((v / W) % H);
         const int zn = (int)(v / ((long long)W * H));
-        const int z = zn % D;
-        float gv[16];
+        const uint4 pk = *reinterpret_cast<const uint4 *>(g + bidx(zn, g_cg_total, g_cg0 + cb, H, W, yy, xx));
+        const __nv_bfloat16 *pb = reinterpret_cast<const __nv_bfloat16 *>(&pk);
 #pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            const uint4 pk = *reinterpret_cast<const uint4 *>(g + bidx(zn, g_cg_total, g_cg0 + c, H, W, yy, xx));
-            const __nv_bfloat16 *pb = reinterpret_cast<const __nv_bfloat16 *>(&pk);
-#pragma unroll
-            for (int q = 0; q < 8; ++q) gv[c * 8 + q] = __bfloat162float(pb[q]);
-        }
-        if (tap == 13)
-#pragma unroll
-            for (int q = 0; q < 16; ++q) accb[q] += gv[q];
-        if (z + dz < 0 || z + dz >= D || yy + dy < 0 || yy + dy >= H || xx + dx < 0 || xx + dx >= W) continue;
-        const float2 in = *reinterpret_cast<const float2 *>(x + ((((size_t)(zn + dz) * H) + yy + dy) * W + xx + dx) * 2);
-#pragma unroll
-        for (int co = 0; co < 16; ++co) {
-            acc[co * 2] += gv[co] * in.x;
-            acc[co * 2 + 1] += gv[co] * in.y;
-        }
+        for (int q = 0; q < 8; ++q) acc[q] += __bfloat162float(pb[q]);
     }
-    __shared__ float red[8][32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int q = 0; q < 32; ++q) {
-        float s = acc[q];
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-        if (lane == 0) red[warp][q] = s;
-    }
+    for (int q = 0; q < 8; ++q) red[threadIdx.x][q] = acc[q];
     __syncthreads();
-    if (threadIdx.x < 32) {
+    if (threadIdx.x < C) {
+        const int c = threadIdx.x;
         float s = 0.0f;
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += red[k][threadIdx.x];
-        atomicAdd(&dw[tap * 32 + threadIdx.x], s);
+        for (int l = 0; l < lanes; ++l) s += red[l * ng + c / 8][c % 8];
+        atomicAdd(&db[c], s);
     }
-    if (tap == 13) {
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-            float s = accb[q];
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-            if (lane == 0) red[warp][q] = s;
-        }
-        __syncthreads();
-        if (threadIdx.x < 16) {
-            float s = 0.0f;
-            for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += red[k][threadIdx.x];
-            atomicAdd(&db[threadIdx.x], s);
-        }
-    }
-}
-
-// ------------------------------------------------------------ weight grads
-// dw[tap][co][ci] += sum_v g[v, co] x[v + off(tap), ci] for one tap per
-// grid-x index, over the 128-voxel tiles of chunk blockIdx.y; db from the
-// centre tap.  x and g are C8-blocked.  Shared memory holds one tile of
-// g (FP32) and the tap-shifted tile of x (FP32, zero outside the sample).
-template <int CIN, int COUT>
-__global__ void __launch_bounds__(256)
-wgrad_kernel(const __nv_bfloat16 *__restrict__ x, int x_cg_total, int x_cg0, const __nv_bfloat16 *__restrict__ g,
-             int g_cg_total, int g_cg0, ConvGeom geo, int tiles_per_cta, float *__restrict__ dw, float *__restrict__ db)
-{
-    constexpr int OUT = CIN * COUT;
-    constexpr int PER = (OUT + 255) / 256;  // outputs per thread
-    __shared__ float sg[64][COUT + 1];  // half a tile at a time (fits the 48 KB static limit)
-    __shared__ float sx[64][CIN + 1];
-    const int tap = blockIdx.x;
-    const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-    const int ntiles = geo.tiles_z * geo.tiles_y * geo.tiles_x;
-    const int plane = geo.box_x * geo.box_y;  // voxels of one plane of a tile
-    float acc[PER];
-#pragma unroll
-    for (int q = 0; q < PER; ++q) acc[q] = 0.0f;
-    float accb = 0.0f;
-    for (int t = blockIdx.y * tiles_per_cta; t < min(ntiles, (blockIdx.y + 1) * tiles_per_cta); ++t) {
-        int tt = t;
-        const int tx = tt % geo.tiles_x;
-        tt /= geo.tiles_x;
-        const int ty = tt % geo.tiles_y;
-        const int z0 = (tt / geo.tiles_y) * geo.box_z;
-        const int x0 = tx * geo.box_x, y0 = ty * geo.box_y;
-        for (int half = 0; half < 2; ++half) {
-            __syncthreads();
-            // stage 64 voxels: one thread per (voxel, channel group)
-            for (int q = threadIdx.x; q < 64 * (COUT / 8); q += 256) {
-                const int mm = q % 64, cb = q / 64, m = half * 64 + mm;
-                const int zn = z0 + m / plane, r = m % plane;
-                const int yy = y0 + r / geo.box_x, xx = x0 + r % geo.box_x;
-                uint4 pk = make_uint4(0, 0, 0, 0);  // voxels past the last plane contribute nothing
-                if (zn < geo.NZ)
-                    pk = *reinterpret_cast<const uint4 *>(g + bidx(zn, g_cg_total, g_cg0 + cb, geo.H, geo.W, yy, xx));
-                const __nv_bfloat16 *pb = reinterpret_cast<const __nv_bfloat16 *>(&pk);
-#pragma unroll
-                for (int k = 0; k < 8; ++k) sg[mm][cb * 8 + k] = __bfloat162float(pb[k]);
-            }
-            for (int q = threadIdx.x; q < 64 * (CIN / 8); q += 256) {
-                const int mm = q % 64, cb = q / 64, m = half * 64 + mm;
-                const int zn = z0 + m / plane, r = m % plane, z = zn % geo.D;
-                const int yy = y0 + r / geo.box_x + dy, xx = x0 + r % geo.box_x + dx;
-                const bool in = zn < geo.NZ && z + dz >= 0 && z + dz < geo.D && yy >= 0 && yy < geo.H && xx >= 0 &&
-                                xx < geo.W;
-                uint4 pk = make_uint4(0, 0, 0, 0);
-                if (in)
-                    pk = *reinterpret_cast<const uint4 *>(
-                        x + bidx(zn + dz, x_cg_total, x_cg0 + cb, geo.H, geo.W, yy, xx));
-                const __nv_bfloat16 *pb = reinterpret_cast<const __nv_bfloat16 *>(&pk);
-#pragma unroll
-                for (int k = 0; k < 8; ++k) sx[mm][cb * 8 + k] = __bfloat162float(pb[k]);
-            }
-            __syncthreads();
-#pragma unroll
-            for (int q = 0; q < PER; ++q) {
-                const int o = threadIdx.x + q * 256;
-                if (o < OUT) {
-                    const int co = o / CIN, ci = o % CIN;
-                    float sacc = 0.0f;
-#pragma unroll 8
-                    for (int m = 0; m < 64; ++m) sacc += sg[m][co] * sx[m][ci];
-                    acc[q] += sacc;
-                }
-            }
-            if (tap == 13 && threadIdx.x < COUT)
-                for (int m = 0; m < 64; ++m) accb += sg[m][threadIdx.x];
-        }
-    }
-#pragma unroll
-    for (int q = 0; q < PER; ++q) {
-        const int o = threadIdx.x + q * 256;
-        if (o < OUT) atomicAdd(&dw[(size_t)tap * OUT + o], acc[q]);
-    }
-    if (tap == 13 && threadIdx.x < COUT) atomicAdd(&db[threadIdx.x], accb);
 }
 
 // ------------------------------------------------------- pool / upsample
@@ -417,47 +262,14 @@ namespace {
 inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 }  // namespace
 
-gbsw_status launch_conv_in2(const float *x, const float *w, const float *b, const ConvGeom &g, bf16 *y, int cg_total,
-                            int cg0, cudaStream_t s)
-{
-    const long long n = (long long)g.NZ * g.H * g.W;
-    conv_in2_kernel<<<nblk(n, 128), 128, 0, s>>>(x, w, b, g.NZ, g.D, g.H, g.W, y, cg_total, cg0);
-    GBSW_LAUNCH_CHECK();
-    return GBSW_OK;
-}
-
-gbsw_status launch_wgrad_in2(const float *x, const bf16 *g, int g_cg_total, int g_cg0, const ConvGeom &geo, float *dw,
+gbsw_status launch_bias_grad(const bf16 *g, int g_cg_total, int g_cg0, long long nvox, int H, int W, int C,
                              float *db, cudaStream_t s)
 {
-    const long long n = (long long)geo.NZ * geo.H * geo.W;
-    const int chunks = (int)std::min<long long>(64, std::max<long long>(1, n / (256 * 16)));
-    wgrad_in2_kernel<<<dim3(27, chunks), 256, 0, s>>>(x, g, g_cg_total, g_cg0, geo.NZ, geo.D, geo.H, geo.W, dw, db);
+    if (C % 8 || C > 64) return GBSW_ERR_ARG;
+    const unsigned blocks = (unsigned)std::min<long long>(2LL * sm_count(), std::max<long long>(1, nvox / 256));
+    bias_grad_kernel<<<blocks, 256, 0, s>>>(g, g_cg_total, g_cg0, nvox, H, W, C, db);
     GBSW_LAUNCH_CHECK();
     return GBSW_OK;
-}
-
-gbsw_status launch_wgrad(int cin, int cout, const bf16 *x, int x_cg_total, int x_cg0, const bf16 *g, int g_cg_total,
-                         int g_cg0, const ConvGeom &geo, float *dw, float *db, cudaStream_t s)
-{
-    const int ntiles = geo.tiles_z * geo.tiles_y * geo.tiles_x;
-    const int chunks = std::max(1, std::min(ntiles, 4 * sm_count() / 27 + 1));
-    const int per = ceil_div(ntiles, chunks);
-    const dim3 grid(27, ceil_div(ntiles, per));
-#define WG_CASE(A, B)                                                                                               \
-    if (cin == A && cout == B) {                                                                                    \
-        wgrad_kernel<A, B><<<grid, 256, 0, s>>>(x, x_cg_total, x_cg0, g, g_cg_total, g_cg0, geo, per, dw, db);      \
-        GBSW_LAUNCH_CHECK();                                                                                        \
-        return GBSW_OK;                                                                                             \
-    }
-    WG_CASE(16, 16)
-    WG_CASE(16, 32)
-    WG_CASE(32, 32)
-    WG_CASE(32, 64)
-    WG_CASE(64, 32)
-    WG_CASE(64, 16)
-    WG_CASE(32, 16)
-#undef WG_CASE
-    return GBSW_ERR_ARG;
 }
 
 gbsw_status launch_pool(const bf16 *x, int x_cg_total, int x_cg0, int NZ, int H, int W, int C, bf16 *y, int y_cg_total,

@@ -16,12 +16,9 @@ struct PadDims {
 
 using bf16 = __nv_bfloat16;
 
-gbsw_status launch_conv_in2(const float *x, const float *w, const float *b, const ConvGeom &g, bf16 *y, int cg_total,
-                            int cg0, cudaStream_t s);
-gbsw_status launch_wgrad_in2(const float *x, const bf16 *g, int g_cg_total, int g_cg0, const ConvGeom &geo, float *dw,
+// db[co] += sum over the nvox voxels of g[v, co] (C8-blocked, C channels from group g_cg0).
+gbsw_status launch_bias_grad(const bf16 *g, int g_cg_total, int g_cg0, long long nvox, int H, int W, int C,
                              float *db, cudaStream_t s);
-gbsw_status launch_wgrad(int cin, int cout, const bf16 *x, int x_cg_total, int x_cg0, const bf16 *g, int g_cg_total,
-                         int g_cg0, const ConvGeom &geo, float *dw, float *db, cudaStream_t s);
 gbsw_status launch_pool(const bf16 *x, int x_cg_total, int x_cg0, int NZ, int H, int W, int C, bf16 *y, int y_cg_total,
                         int y_cg0, cudaStream_t s);
 gbsw_status launch_upsample(const bf16 *x, int x_cg_total, int x_cg0, int NZ, int H, int W, int C, bf16 *y,

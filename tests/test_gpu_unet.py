@@ -1,16 +1,22 @@
 """The GPU U-Net (tcgen05 convolutions, BF16 activations, FP32 accumulation)
 against the FP64 oracle network with the same parameters.
 
-BF16 rounding of every activation bounds the agreement: relative L2 error of
-the output <= 3e-2, gradients aligned (cosine >= 0.99) and within 10 % per
-layer.  Training must reduce the loss; the LES with the network as warm
-start still converges to the same tolerance (the solve decides the answer).
+Against the BF16-faithful FP64 network (tests/unet_bf16.py: the oracle's
+operators, rounded to BF16 where the GPU stores BF16) the output must agree
+to a relative L2 error of 1e-2 and every layer's gradients to 1e-2; only the
+FP32 summation order separates the two.  Against the plain FP64 oracle,
+which rounds nothing, the BF16 storage of the activations accounts for a
+few per cent (output <= 3e-2, gradients aligned).  Training must reduce the
+loss; the LES with the network as warm start still converges to the same
+tolerance (the solve decides the answer).
 """
 import numpy as np
 import pytest
 
 import oracle
 from oracle import unet as OU
+
+import unet_bf16 as UB
 
 pytestmark = pytest.mark.gpu
 
@@ -43,30 +49,50 @@ def test_forward_matches_oracle(U):
         P = U.unflatten(bf16(net.get_params()).astype(np.float64))
         net.set_params(U.flatten(P))
         y = net.forward(torch.from_numpy(x).cuda()).cpu().numpy()
+    want, _ = UB.forward(P, x.astype(np.float64))
+    err = np.linalg.norm(y - want) / np.linalg.norm(want)
+    print(f"network output vs BF16-faithful FP64 network: rel-L2 {err:.2e}")
+    assert err <= 1e-2, err
     for k in range(2):
         ref, _ = OU.forward(P, x[k].astype(np.float64))
-        err = np.linalg.norm(y[k] - ref[..., 0]) / np.linalg.norm(ref)
-        assert err <= 3e-2, err
+        assert np.linalg.norm(y[k] - ref[..., 0]) / np.linalg.norm(ref) <= 3e-2
 
 
-def test_gradients_match_oracle(U):
+@pytest.mark.parametrize("shape", [(1, 4, 32, 64), (4, 8, 16, 16)])
+def test_gradients_match_oracle(U, shape):
+    """Every layer's weight and bias gradients (tcgen05 weight gradients,
+    backward-data with flipped weights) against the BF16-faithful FP64
+    network at 1e-2 relative; the second shape is the warm-start training
+    batch geometry (coarse 8 x 16 x 16 grids: multi-plane tiles at the
+    coarse levels, tiles that cross samples)."""
     import torch
     rng = np.random.default_rng(1)
-    x, t = sample(rng, 1, 4, 32, 64)
+    x, t = sample(rng, *shape)
     with U.UNet(seed=5) as net:
         P = U.unflatten(bf16(net.get_params()).astype(np.float64))
         net.set_params(U.flatten(P))
         loss, g = net.gradients(torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda())
-    out, c = OU.forward(P, x[0].astype(np.float64))
-    lo, dout = OU.mse(out, t[0][..., None].astype(np.float64))
-    Go = OU.backward(P, c, dout)
-    assert abs(loss - lo) <= 3e-2 * lo
+    _, c = UB.forward(P, x.astype(np.float64))
+    lo, Gb = UB.backward(P, c, t.astype(np.float64))
+    assert abs(loss - lo) <= 1e-2 * lo
     Gg = U.unflatten(g.astype(np.float64))
-    for name in Go:
-        a, b = Gg[name].ravel(), Go[name].ravel()
-        cos = a @ b / (np.linalg.norm(a) * np.linalg.norm(b) + 1e-300)
-        rel = np.linalg.norm(a - b) / (np.linalg.norm(b) + 1e-300)
-        assert cos >= 0.99 and rel <= 0.1, (name, cos, rel)
+    errs = {}
+    for name in Gb:
+        a, b = Gg[name].ravel(), np.asarray(Gb[name]).ravel()
+        errs[name] = np.linalg.norm(a - b) / (np.linalg.norm(b) + 1e-300)
+    print("per-layer gradient rel-L2 vs BF16-faithful FP64 network: " +
+          " ".join(f"{k} {v:.1e}" for k, v in errs.items()))
+    for name, r in errs.items():
+        assert r <= 1e-2, (name, r)
+    # and against the plain FP64 oracle, which stores nothing in BF16
+    if shape[0] == 1:
+        out, co = OU.forward(P, x[0].astype(np.float64))
+        lo64, dout = OU.mse(out, t[0][..., None].astype(np.float64))
+        Go = OU.backward(P, co, dout)
+        for name in Go:
+            a, b = Gg[name].ravel(), Go[name].ravel()
+            cos = a @ b / (np.linalg.norm(a) * np.linalg.norm(b) + 1e-300)
+            assert cos >= 0.99, (name, cos)
 
 
 def test_training_reduces_loss(U):
