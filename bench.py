@@ -652,6 +652,7 @@ def run_sw_paper(args, rank, world, local):
     for n in (500, 1000, 2000):
         inp = inputs.sw_hump(n=n, dx=1.0, dt=0.01, sigma_cells=n / 20.0)
         with SW(inp.params(), inp.H, inp.eta0, stream=torch.cuda.current_stream()) as g:
+            tiling = g.autotune(trial_steps=120)
             g.step(300)
             g.volume()
             t = _timed_region(lambda: (g.step(10000), g.volume()), world)
@@ -668,6 +669,7 @@ def run_sw_paper(args, rank, world, local):
                 oracle.use_openmp(False)
             cpu["threads"] = oracle.threads()
         res.append({"n": n, "seconds_10000_steps": t, "cell_updates_per_s": n * n * 10000 / t,
+                    "tiling": {"steps_per_launch": tiling[0], "rows_per_block": tiling[1]},
                     "oracle_cell_updates_per_s_1thread": cpu.get(False),
                     "oracle_cell_updates_per_s_all_cores": cpu.get(True), "oracle_threads": cpu.get("threads")})
     if rank != 0:

@@ -148,8 +148,24 @@ gbsw_status sw_get_state(gbsw_sw *sw, float *eta, float *u, float *v, uint8_t *w
 gbsw_status sw_set_state(gbsw_sw *sw, const float *eta, const float *u, const float *v);
 
 /* Number of time steps fused per kernel launch (temporal blocking depth):
- * 0 = automatic, else 1..6. */
+ * 0 = automatic, else 1..6 (the row-segment height returns to automatic). */
 gbsw_status sw_set_blocking(gbsw_sw *sw, int steps_per_launch);
+
+/* Tiling of the fused kernel: steps per launch (0 = automatic, else 1..6)
+ * and the row-segment height of a thread block (0 = automatic: one wave of
+ * resident blocks, segments of at least 8T rows).  Results do not depend
+ * on the tiling (every operation is rounded as written). */
+gbsw_status sw_set_tiling(gbsw_sw *sw, int steps_per_launch, int rows);
+
+/* Choose the tiling by measurement: times trial_steps (1..100000, rounded
+ * to whole launches) on the context's own state for each depth T = 1..6
+ * and row-segment heights giving the default, one, two and three waves of
+ * resident blocks, keeps the fastest (written to *T_out, *rows_out if
+ * non-NULL) and restores the state exactly.  Allocates a copy of the state;
+ * synchronous.  The paper's grids (Sec. 6.2: 500^2 to 2000^2) are small
+ * enough to stay in L2, where the best tiling differs from the 4096^2
+ * default. */
+gbsw_status sw_autotune(gbsw_sw *sw, int trial_steps, int *T_out, int *rows_out);
 
 /* Release the context and its device memory.  NULL is ignored. */
 void sw_destroy(gbsw_sw *sw);

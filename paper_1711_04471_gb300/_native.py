@@ -56,6 +56,8 @@ def _declare(L):
     _sig(L, "sw_get_state", C.c_int, [_vp, _fp, _fp, _fp, C.POINTER(C.c_uint8)])
     _sig(L, "sw_set_state", C.c_int, [_vp, _fp, _fp, _fp])
     _sig(L, "sw_set_blocking", C.c_int, [_vp, C.c_int])
+    _sig(L, "sw_set_tiling", C.c_int, [_vp, C.c_int, C.c_int])
+    _sig(L, "sw_autotune", C.c_int, [_vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)])
     _sig(L, "sw_destroy", None, [_vp])
     _sig(L, "sw64_create", C.c_int, [C.POINTER(SWParams), _dp, _dp, _vp, C.POINTER(_vp)])
     _sig(L, "sw64_step", C.c_int, [_vp, C.c_int])

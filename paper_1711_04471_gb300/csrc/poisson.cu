@@ -59,6 +59,12 @@ __global__ void __launch_bounds__(SOR_THREADS)
 sor_sweep_kernel(PDims d, int colour, float omega, float h2, SorDiag dg, float *__restrict__ ec,
                  const float *__restrict__ eo, const float *__restrict__ rc)
 {
+    // Programmatic dependent launch: the next half-sweep may be scheduled
+    // as soon as every block of this one has started, and this one reads
+    // nothing before the previous grid has completed and its writes are
+    // visible (both are no-ops for a launch without that dependency).
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     int j, s0;
     if (FLAT) {
         const int ngroups = ((d.nx + 1) / 2 + 3) >> 2;
@@ -269,17 +275,44 @@ static dim3 sweep_grid(const PDims &d)
     return dim3(ceil_div(ngroups, 32), ceil_div(d.ny, SOR_THREADS / 32), ceil_div(d.nz, SOR_KZ));
 }
 
-// Enqueue one colour half-sweep.
+// Enqueue one colour half-sweep.  after_sweep: the previous launch on the
+// stream is a half-sweep, so this one may start programmatically (its
+// blocks are scheduled during the previous sweep's last wave and wait in
+// griddepcontrol.wait for its completion).
 template <bool FIRST>
-static void launch_sweep(const PDims &d, int colour, float om, float h2, float *ec, const float *eo, const float *rc,
-                         cudaStream_t s)
+static cudaError_t launch_sweep(const PDims &d, int colour, float om, float h2, float *ec, const float *eo,
+                                const float *rc, cudaStream_t s, bool after_sweep)
 {
-    const dim3 g = sweep_grid(d);
     const SorDiag dg = sor_diag();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = sweep_grid(d);
+    cfg.blockDim = dim3(SOR_THREADS);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = after_sweep ? attr : nullptr;
+    cfg.numAttrs = after_sweep ? 1 : 0;
     if (sweep_flat(d))
-        sor_sweep_kernel<FIRST, true><<<g, SOR_THREADS, 0, s>>>(d, colour, om, h2, dg, ec, eo, rc);
-    else
-        sor_sweep_kernel<FIRST, false><<<g, SOR_THREADS, 0, s>>>(d, colour, om, h2, dg, ec, eo, rc);
+        return cudaLaunchKernelEx(&cfg, sor_sweep_kernel<FIRST, true>, d, colour, om, h2, dg, ec, eo, rc);
+    return cudaLaunchKernelEx(&cfg, sor_sweep_kernel<FIRST, false>, d, colour, om, h2, dg, ec, eo, rc);
+}
+
+// m red-black iterations, the first from e = 0 (FIRST).
+static cudaError_t launch_iterations(const PDims &d, int m, float om, float h2, float *const e[2],
+                                     float *const r[2], cudaStream_t s)
+{
+    cudaError_t err = cudaSuccess;
+    for (int it = 0; it < m && err == cudaSuccess; ++it) {
+        if (it == 0) {
+            err = launch_sweep<true>(d, 0, om, h2, e[0], e[1], r[0], s, false);
+            if (err == cudaSuccess) err = launch_sweep<true>(d, 1, om, h2, e[1], e[0], r[1], s, true);
+        } else {
+            err = launch_sweep<false>(d, 0, om, h2, e[0], e[1], r[0], s, true);
+            if (err == cudaSuccess) err = launch_sweep<false>(d, 1, om, h2, e[1], e[0], r[1], s, true);
+        }
+    }
+    return err;
 }
 
 gbsw_status PoissonSolver::init(int nx, int ny, int nz, double dx, const float *b_dev, cudaStream_t s)
@@ -404,12 +437,7 @@ gbsw_status PoissonSolver::build_graph()
         body = cp.conditional.phGraph_out[0];
         chk(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
         if (err == cudaSuccess) {
-            launch_sweep<true>(d, 0, om, h2, e[0], e[1], r[0], cs);
-            launch_sweep<true>(d, 1, om, h2, e[1], e[0], r[1], cs);
-            for (int it = 1; it < m; ++it) {
-                launch_sweep<false>(d, 0, om, h2, e[0], e[1], r[0], cs);
-                launch_sweep<false>(d, 1, om, h2, e[1], e[0], r[1], cs);
-            }
+            chk(launch_iterations(d, m, om, h2, e, r, cs));
             poisson_fold_kernel<<<fgrid, fblock, 0, cs>>>(d, 0, p_hi, e[0]);
             poisson_fold_kernel<<<fgrid, fblock, 0, cs>>>(d, 1, p_hi, e[1]);
             poisson_resid_kernel<false><<<rgrid, POI_RED_THREADS, 0, cs>>>(d, b, p_hi, r[0], r[1], partials);
@@ -480,14 +508,10 @@ gbsw_status PoissonSolver::record_fixed(int niter, cudaStream_t stream)
     GBSW_CUDA_TRY(cudaMemsetAsync(e[1], 0, nc * sizeof(float), stream));
     poisson_resid_kernel<true><<<rgrid, POI_RED_THREADS, 0, stream>>>(d, b, p_hi, r[0], r[1], partials);
     poisson_test_kernel<false><<<1, POI_RED_THREADS, 0, stream>>>(partials, rblocks, ctl, 0.0, niter, 0, 0, 0);
-    for (int it = 0; it < niter; ++it) {
-        if (it == 0) {
-            launch_sweep<true>(d, 0, om, h2, e[0], e[1], r[0], stream);
-            launch_sweep<true>(d, 1, om, h2, e[1], e[0], r[1], stream);
-        } else {
-            launch_sweep<false>(d, 0, om, h2, e[0], e[1], r[0], stream);
-            launch_sweep<false>(d, 1, om, h2, e[1], e[0], r[1], stream);
-        }
+    cudaError_t err = launch_iterations(d, niter, om, h2, e, r, stream);
+    if (err != cudaSuccess) {
+        record_cuda_error(err, "SOR sweep launch", __FILE__, __LINE__);
+        return GBSW_ERR_CUDA;
     }
     poisson_fold_kernel<<<fgrid, fblock, 0, stream>>>(d, 0, p_hi, e[0]);
     poisson_fold_kernel<<<fgrid, fblock, 0, stream>>>(d, 1, p_hi, e[1]);

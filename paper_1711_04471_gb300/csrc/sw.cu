@@ -90,6 +90,11 @@ struct gbsw_sw {
     float *eta[2], *u[2], *v[2];
     int cur;
     int blocking;           // 0 = automatic
+    int rows;               // row-segment height of a CTA, 0 = automatic
+    // CUDA graphs of SW_CHUNK fused launches of depth chunk_T starting from
+    // buffer set 0 or 1, replayed by sw_step (rebuilt when the tiling changes)
+    cudaGraphExec_t chunk[2];
+    int chunk_T, chunk_rows;
     double *partials;       // SW_VOL_BLOCKS * 3 doubles (scratch of the volume reduction)
     double *result;         // 3 doubles on the device
     double *h_result;       // 3 doubles, pinned host
@@ -98,52 +103,152 @@ struct gbsw_sw {
 
 namespace {
 
-// Streaming launch of depth T: one wave of CTAs sized from the occupancy so
-// that every resident CTA gets one (strip, row segment) of equal height.
+constexpr int SW_CHUNK = 32;  // fused launches per replayed graph (even: a chunk ends on its start buffer)
+
+// Resident CTAs per SM of the depth-T streaming kernel.
 template <int T>
-cudaError_t launch_stream(const gbsw_sw *s, const float *eta_in, const float *u_in, const float *v_in,
-                          float *eta_out, float *u_out, float *v_out)
+int stream_per_sm()
 {
     static int per_sm = 0;
     if (per_sm == 0) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sw_stream_kernel<T>, SWS_THREADS, 0);
-        if (e != cudaSuccess) return e;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sw_stream_kernel<T>, SWS_THREADS, 0) !=
+            cudaSuccess)
+            per_sm = 0;
         if (per_sm < 1) per_sm = 1;
     }
+    return per_sm;
+}
+
+int stream_per_sm(int T)
+{
+    switch (T) {
+    case 1: return stream_per_sm<1>();
+    case 2: return stream_per_sm<2>();
+    case 3: return stream_per_sm<3>();
+    case 4: return stream_per_sm<4>();
+    case 5: return stream_per_sm<5>();
+    default: return stream_per_sm<6>();
+    }
+}
+
+// Default row-segment height: one wave of CTAs sized from the occupancy,
+// every resident CTA one (strip, row segment), with segments kept well
+// above the pipeline depth (3T - 1 rows of fill per segment).
+int default_rows(const gbsw_sw *s, int T)
+{
+    const int strips = ceil_div(s->d.nx, SWS_THREADS - 4 * T);
+    const int capacity = stream_per_sm(T) * sm_count();
+    int segments = std::max(1, capacity / strips);
+    segments = std::min(segments, std::max(1, s->d.ny / (8 * T)));
+    return ceil_div(s->d.ny, segments);
+}
+
+// Streaming launch of depth T over row segments of `rows` rows.
+template <int T>
+cudaError_t launch_stream(const gbsw_sw *s, int rows, cudaStream_t st, const float *eta_in, const float *u_in,
+                          const float *v_in, float *eta_out, float *u_out, float *v_out)
+{
     constexpr int W = SWS_THREADS - 4 * T;
     const int strips = ceil_div(s->d.nx, W);
-    const int capacity = per_sm * sm_count();
-    int segments = std::max(1, capacity / strips);
-    segments = std::min(segments, std::max(1, s->d.ny / (8 * T)));  // keep segments >> the pipeline depth
-    const int rows = ceil_div(s->d.ny, segments);
-    segments = ceil_div(s->d.ny, rows);
+    const int segments = ceil_div(s->d.ny, rows);
     dim3 grid(strips, segments);
-    sw_stream_kernel<T><<<grid, SWS_THREADS, 0, s->stream>>>(s->d, rows, s->H, eta_in, u_in, v_in, eta_out,
-                                                            u_out, v_out);
+    sw_stream_kernel<T><<<grid, SWS_THREADS, 0, st>>>(s->d, rows, s->H, eta_in, u_in, v_in, eta_out, u_out, v_out);
     return cudaGetLastError();
 }
 
-// One launch of depth T from buffer `cur` into the other buffer set.
-cudaError_t sw_launch(gbsw_sw *s, int T)
+// One launch of depth T from buffer set a into the other one, on stream st.
+cudaError_t launch_from(const gbsw_sw *s, int T, int rows, int a, cudaStream_t st)
 {
-    const int a = s->cur, b = 1 - s->cur;
-    cudaError_t e;
+    const int b = 1 - a;
     const float *ei = s->eta[a], *ui = s->u[a], *vi = s->v[a];
     float *eo = s->eta[b], *uo = s->u[b], *vo = s->v[b];
     switch (T) {
-    case 1: e = launch_stream<1>(s, ei, ui, vi, eo, uo, vo); break;
-    case 2: e = launch_stream<2>(s, ei, ui, vi, eo, uo, vo); break;
-    case 3: e = launch_stream<3>(s, ei, ui, vi, eo, uo, vo); break;
-    case 4: e = launch_stream<4>(s, ei, ui, vi, eo, uo, vo); break;
-    case 5: e = launch_stream<5>(s, ei, ui, vi, eo, uo, vo); break;
-    case 6: e = launch_stream<6>(s, ei, ui, vi, eo, uo, vo); break;
+    case 1: return launch_stream<1>(s, rows, st, ei, ui, vi, eo, uo, vo);
+    case 2: return launch_stream<2>(s, rows, st, ei, ui, vi, eo, uo, vo);
+    case 3: return launch_stream<3>(s, rows, st, ei, ui, vi, eo, uo, vo);
+    case 4: return launch_stream<4>(s, rows, st, ei, ui, vi, eo, uo, vo);
+    case 5: return launch_stream<5>(s, rows, st, ei, ui, vi, eo, uo, vo);
+    case 6: return launch_stream<6>(s, rows, st, ei, ui, vi, eo, uo, vo);
     default: return cudaErrorInvalidValue;
     }
-    if (e == cudaSuccess) s->cur = b;
-    return e;
 }
 
 int auto_blocking(const gbsw_sw *) { return 3; }
+
+int tiling_T(const gbsw_sw *s) { return s->blocking > 0 ? s->blocking : auto_blocking(s); }
+
+int tiling_rows(const gbsw_sw *s, int T) { return s->rows > 0 ? s->rows : default_rows(s, T); }
+
+void drop_chunks(gbsw_sw *s)
+{
+    for (int k = 0; k < 2; ++k) {
+        if (s->chunk[k]) cudaGraphExecDestroy(s->chunk[k]);
+        s->chunk[k] = nullptr;
+    }
+}
+
+// The graph of SW_CHUNK launches of depth T starting from buffer set a
+// (captured on a private stream, replayed on the context's stream).
+cudaError_t chunk_graph(gbsw_sw *s, int T, int rows, int a, cudaGraphExec_t *out)
+{
+    if (s->chunk_T != T || s->chunk_rows != rows) {
+        drop_chunks(s);
+        s->chunk_T = T;
+        s->chunk_rows = rows;
+    }
+    if (s->chunk[a]) {
+        *out = s->chunk[a];
+        return cudaSuccess;
+    }
+    cudaStream_t cs = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    cudaGraph_t g = nullptr;
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t el = cudaSuccess;
+        for (int k = 0; k < SW_CHUNK && el == cudaSuccess; ++k) el = launch_from(s, T, rows, (a + k) & 1, cs);
+        e = cudaStreamEndCapture(cs, &g);
+        if (e == cudaSuccess) e = el;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&s->chunk[a], g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+        s->chunk[a] = nullptr;
+        return e;
+    }
+    *out = s->chunk[a];
+    return cudaSuccess;
+}
+
+// nsteps time steps with depth-T launches over `rows`-row segments: whole
+// chunks of SW_CHUNK launches as graph replays, the rest launched directly.
+gbsw_status run_steps(gbsw_sw *s, int nsteps, int T, int rows)
+{
+    int full = nsteps / T;
+    const int rest = nsteps % T;
+    while (full >= SW_CHUNK) {
+        cudaGraphExec_t ge = nullptr;
+        cudaError_t e = chunk_graph(s, T, rows, s->cur, &ge);
+        if (e == cudaSuccess) e = cudaGraphLaunch(ge, s->stream);
+        if (e != cudaSuccess) {
+            record_cuda_error(e, "sw_step graph", __FILE__, __LINE__);
+            return GBSW_ERR_CUDA;
+        }
+        full -= SW_CHUNK;  // even: the chunk ends on the buffer set it started from
+    }
+    for (int k = 0; k < full + (rest > 0); ++k) {
+        const int t = k < full ? T : rest;
+        cudaError_t e = launch_from(s, t, t == T ? rows : default_rows(s, t), s->cur, s->stream);
+        if (e != cudaSuccess) {
+            record_cuda_error(e, "sw_stream_kernel", __FILE__, __LINE__);
+            return GBSW_ERR_CUDA;
+        }
+        s->cur = 1 - s->cur;
+    }
+    return GBSW_OK;
+}
 
 }  // namespace
 
@@ -233,6 +338,15 @@ gbsw_status sw_set_blocking(gbsw_sw *s, int steps_per_launch)
 {
     if (!s || steps_per_launch < 0 || steps_per_launch > SW_MAX_BLOCKING) return GBSW_ERR_ARG;
     s->blocking = steps_per_launch;
+    s->rows = 0;
+    return GBSW_OK;
+}
+
+gbsw_status sw_set_tiling(gbsw_sw *s, int steps_per_launch, int rows)
+{
+    if (!s || steps_per_launch < 0 || steps_per_launch > SW_MAX_BLOCKING || rows < 0) return GBSW_ERR_ARG;
+    s->blocking = steps_per_launch;
+    s->rows = rows;
     return GBSW_OK;
 }
 
@@ -240,17 +354,81 @@ gbsw_status sw_step(gbsw_sw *s, int nsteps)
 {
     gbsw::NvtxRange nvtx_range("sw_step");
     if (!s || nsteps < 0) return GBSW_ERR_ARG;
-    const int T = s->blocking > 0 ? s->blocking : auto_blocking(s);
-    int left = nsteps;
-    while (left > 0) {
-        int t = std::min(left, T);
-        cudaError_t e = sw_launch(s, t);
-        if (e != cudaSuccess) {
-            record_cuda_error(e, "sw_fused_kernel", __FILE__, __LINE__);
-            return GBSW_ERR_CUDA;
+    const int T = tiling_T(s);
+    return run_steps(s, nsteps, T, tiling_rows(s, T));
+}
+
+gbsw_status sw_autotune(gbsw_sw *s, int trial_steps, int *T_out, int *rows_out)
+{
+    gbsw::NvtxRange nvtx_range("sw_autotune");
+    if (!s || trial_steps < 1 || trial_steps > 100000) return GBSW_ERR_ARG;
+    const size_t fb = (size_t)s->d.pitch * (size_t)s->d.ny * sizeof(float);
+    float *save[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    gbsw_status st = GBSW_OK;
+    int bestT = tiling_T(s), best_rows = tiling_rows(s, bestT);
+    float best = INFINITY;
+    const int c0 = s->cur;
+    do {
+        bool ok = true;
+        for (int k = 0; k < 3 && ok; ++k) ok = cudaMalloc((void **)&save[k], fb) == cudaSuccess;
+        if (!ok) {
+            st = GBSW_ERR_OOM;
+            break;
         }
-        left -= t;
-    }
+        if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
+            cudaMemcpyAsync(save[0], s->eta[c0], fb, cudaMemcpyDeviceToDevice, s->stream) != cudaSuccess ||
+            cudaMemcpyAsync(save[1], s->u[c0], fb, cudaMemcpyDeviceToDevice, s->stream) != cudaSuccess ||
+            cudaMemcpyAsync(save[2], s->v[c0], fb, cudaMemcpyDeviceToDevice, s->stream) != cudaSuccess) {
+            st = GBSW_ERR_CUDA;
+            break;
+        }
+        for (int T = 1; T <= SW_MAX_BLOCKING && st == GBSW_OK; ++T) {
+            // segment heights: the default, and those giving 1, 2, 3 waves of resident CTAs
+            const int strips = ceil_div(s->d.nx, SWS_THREADS - 4 * T);
+            const int capacity = stream_per_sm(T) * sm_count();
+            int cand[4] = {default_rows(s, T), 0, 0, 0};
+            for (int w = 1; w <= 3; ++w)
+                cand[w] = std::max(2, ceil_div(s->d.ny, std::max(1, ceil_div(w * capacity, strips))));
+            for (int c = 0; c < 4 && st == GBSW_OK; ++c) {
+                bool seen = false;
+                for (int q = 0; q < c; ++q) seen |= cand[q] == cand[c];
+                if (seen) continue;
+                const int steps = std::max(T, trial_steps / T * T);
+                if ((st = run_steps(s, steps, T, cand[c])) != GBSW_OK) break;  // warm-up (and graph capture)
+                cudaEventRecord(e0, s->stream);
+                if ((st = run_steps(s, steps, T, cand[c])) != GBSW_OK) break;
+                cudaEventRecord(e1, s->stream);
+                float ms = 0.0f;
+                if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                    st = GBSW_ERR_CUDA;
+                    break;
+                }
+                const float per = ms / steps;
+                if (per < best) {
+                    best = per;
+                    bestT = T;
+                    best_rows = cand[c];
+                }
+            }
+        }
+        // restore the state: results do not depend on the tiling, so the
+        // trials leave no trace
+        const int c = s->cur;
+        if (cudaMemcpyAsync(s->eta[c], save[0], fb, cudaMemcpyDeviceToDevice, s->stream) != cudaSuccess ||
+            cudaMemcpyAsync(s->u[c], save[1], fb, cudaMemcpyDeviceToDevice, s->stream) != cudaSuccess ||
+            cudaMemcpyAsync(s->v[c], save[2], fb, cudaMemcpyDeviceToDevice, s->stream) != cudaSuccess ||
+            cudaStreamSynchronize(s->stream) != cudaSuccess)
+            st = GBSW_ERR_CUDA;
+    } while (0);
+    for (int k = 0; k < 3; ++k) cudaFree(save[k]);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st != GBSW_OK) return st;
+    s->blocking = bestT;
+    s->rows = best_rows;
+    if (T_out) *T_out = bestT;
+    if (rows_out) *rows_out = best_rows;
     return GBSW_OK;
 }
 
@@ -326,6 +504,7 @@ void sw_destroy(gbsw_sw *s)
 {
     if (!s) return;
     cudaStreamSynchronize(s->stream);
+    drop_chunks(s);
     cudaFree(s->H);
     for (int b = 0; b < 2; ++b) {
         cudaFree(s->eta[b]);

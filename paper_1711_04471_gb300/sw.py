@@ -34,6 +34,16 @@ class SW:
     def set_blocking(self, T: int) -> None:
         N.check(N.lib().sw_set_blocking(self._h, int(T)), "sw_set_blocking")
 
+    def set_tiling(self, T: int, rows: int) -> None:
+        N.check(N.lib().sw_set_tiling(self._h, int(T), int(rows)), "sw_set_tiling")
+
+    def autotune(self, trial_steps: int = 60):
+        """Pick the fused depth and row-segment height by timing them on this
+        grid (the state is restored); returns (T, rows)."""
+        T, rows = C.c_int(), C.c_int()
+        N.check(N.lib().sw_autotune(self._h, int(trial_steps), C.byref(T), C.byref(rows)), "sw_autotune")
+        return T.value, rows.value
+
     def volume(self):
         v, w = C.c_double(), C.c_double()
         N.check(N.lib().sw_volume(self._h, C.byref(v), C.byref(w)), "sw_volume")

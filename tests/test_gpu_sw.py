@@ -160,6 +160,37 @@ def test_rectangular_ragged_and_tiny(SW):
         assert np.array_equal(st["wet"], o.wet_i)
 
 
+def test_tilings_and_autotune_bitwise(SW):
+    """The fused kernel's result does not depend on its tiling (fusion depth,
+    row-segment height, graph-replayed chunks or direct launches), and the
+    autotuner leaves the state exactly as it found it."""
+    inp = nudge(inputs.sw_wetdry(n=150, seed=8))
+    nsteps = 203                     # whole 32-launch graph chunks plus direct launches and a remainder
+    with SW(inp.params(), inp.H, inp.eta0) as g:
+        g.set_tiling(1, 0)
+        g.step(nsteps)
+        ref = g.get_state()
+    for T, rows in [(2, 3), (3, 7), (4, 150), (6, 2), (5, 40)]:
+        with SW(inp.params(), inp.H, inp.eta0) as g:
+            g.set_tiling(T, rows)
+            g.step(nsteps)
+            got = g.get_state()
+        for f in ("eta", "u", "v", "wet"):
+            assert np.array_equal(got[f], ref[f]), (T, rows, f)
+    with SW(inp.params(), inp.H, inp.eta0) as g:
+        g.step(17)
+        before = g.get_state()
+        T, rows = g.autotune(trial_steps=12)
+        assert 1 <= T <= 6 and rows >= 2
+        after = g.get_state()
+        for f in ("eta", "u", "v", "wet"):
+            assert np.array_equal(before[f], after[f]), f
+        g.step(nsteps - 17)
+        tuned = g.get_state()
+    for f in ("eta", "u", "v", "wet"):
+        assert np.array_equal(tuned[f], ref[f]), f
+
+
 def test_zero_steps_and_set_state_roundtrip(SW):
     inp = inputs.sw_hump(n=40)
     with SW(inp.params(), inp.H, inp.eta0) as g:
