@@ -13,10 +13,10 @@ row of the hot path.  The state (268 MB of eta, u, v, H) is larger than the
 129 MB L2, so no L2 flush is needed between steps.
 
 The same line carries an ``les`` object: the UFLES 256x256x128 step at a
-1e-6 FP64 residual after 20 spin-up steps, the previous-pressure warm start
-and the learned (U-Net) warm start compared on the same 10 states, with
-device times, SOR iterations, end-to-end wall time through les_step and the
-FP64 oracle on the host cores.
+1e-6 FP64 residual over steps 21..200, the previous-pressure warm start and
+the learned (U-Net) warm start compared on the same 10 states spread evenly
+over those steps, with device times, SOR iterations, end-to-end wall time
+through les_step and the FP64 oracle on the host cores.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gbsw|reference]
 
@@ -502,39 +502,45 @@ def l2_copy_gbs(mb=32.0, passes=64):
 
 
 def les_compare(args, solid, shape=LES_SHAPE, log=lambda *a: None):
-    """The UFLES step at the solver tolerance after args.les_spinup steps:
-    from each of args.les_steps states of a previous-pressure run, one step
-    with the previous pressure as warm start and one with the U-Net, both to
-    the same tolerance (device times from the step's own CUDA events).  Then
-    each run continues for args.les_e2e_steps steps timed end to end on the
-    host: les_step plus the read-back of the FP64 pressure to host memory."""
+    """The UFLES step at the solver tolerance over steps spinup+1 ..
+    spinup+horizon: one run advances with the learned (U-Net) warm start,
+    and at `compared` evenly spaced steps its checkpoint is restored into a
+    second context with the previous-pressure warm start, so that both take
+    that step from the same state, to the same tolerance (device times from
+    the step's own CUDA events).  Both solves reach the same 1e-6 residual,
+    so the run's states are those of a previous-pressure run to within the
+    solver tolerance.  Then each context continues for args.les_e2e_steps
+    steps timed end to end on the host: les_step plus the read-back of the
+    FP64 pressure to host memory."""
     import numpy as np
 
     from paper_1711_04471_gb300.les import LES
     from paper_1711_04471_gb300.unet import UNet
     kw = dict(check_every=args.check_every, max_iter=400000)
-    names = ("u", "v", "w", "p", "fuo", "fvo", "fwo", "gu", "gv", "gw")
+    horizon, compared = args.les_horizon, args.les_steps
+    stride = max(1, horizon // max(1, compared))
     rows = []
-    with UNet(seed=0) as net, LES(*shape, solid, **kw) as ref, LES(*shape, solid, **kw) as trial:
+    with UNet(seed=0) as net, LES(*shape, solid, **kw) as run, LES(*shape, solid, **kw) as plain:
         net.set_params(np.load(args.weights))
-        ref.step(args.les_spinup, stats=False)
-        trial.set_warm_start(net)
-        for _ in range(args.les_steps):
-            state = {n: ref.get(n) for n in names}
-            count = ref.step_count
-            for n in names:
-                trial.set(n, state[n])
-            trial.step_count = count
-            a = ref.step(1)[0]
-            b = trial.step(1)[0]
-            rows.append(dict(step=count + 1, plain_iters=a["iters"], nn_iters=b["iters"],
-                             plain_ms=a["ms_predictor"] + a["ms_solve"], plain_pred_ms=a["ms_predictor"],
-                             plain_solve_ms=a["ms_solve"], plain_res=a["rel_res"], plain_status=a["status"],
-                             nn_ms=b["ms_predictor"] + b["ms_guess"] + b["ms_solve"], nn_guess_ms=b["ms_guess"],
-                             nn_solve_ms=b["ms_solve"], nn_res=b["rel_res"], nn_status=b["status"]))
-            log(rows[-1])
+        run.set_warm_start(net)
+        run.step(args.les_spinup, stats=False)
+        for k in range(1, horizon + 1):
+            if k % stride == 0 and len(rows) < compared:
+                state = run.get_state()          # the same state for both warm starts
+                plain.set_state(state)
+                a = plain.step(1)[0]
+                b = run.step(1)[0]
+                rows.append(dict(step=state["step"] + 1, plain_iters=a["iters"], nn_iters=b["iters"],
+                                 plain_ms=a["ms_predictor"] + a["ms_solve"], plain_pred_ms=a["ms_predictor"],
+                                 plain_solve_ms=a["ms_solve"], plain_res=a["rel_res"], plain_status=a["status"],
+                                 nn_ms=b["ms_predictor"] + b["ms_guess"] + b["ms_solve"], nn_guess_ms=b["ms_guess"],
+                                 nn_solve_ms=b["ms_solve"], nn_res=b["rel_res"], nn_status=b["status"]))
+                log(rows[-1])
+            else:
+                run.step(1, stats=False)
         e2e = {}
-        for name, g in (("plain", ref), ("learned", trial)):
+        plain.set_state(run.get_state())
+        for name, g in (("plain", plain), ("learned", run)):
             g.step(1, stats=False)
             t0 = time.perf_counter()
             for _ in range(args.les_e2e_steps):
@@ -572,7 +578,8 @@ def les_object(args, local):
     out = {
         "workload": f"UFLES 256x256x128, dx 4 m, dt 0.025 s, 20 % building cover (building seed {args.les_seed}), "
                     f"SOR omega 1.8 to a 1e-6 relative FP64 residual checked every {args.check_every} iterations; "
-                    f"{args.les_spinup} spin-up steps, then {n} states compared",
+                    f"{args.les_spinup} spin-up steps, then {n} states compared, evenly spaced over steps "
+                    f"{args.les_spinup + 1}..{args.les_spinup + args.les_horizon}",
         "metric": "LES step time at 1e-6 residual, learned vs previous-pressure warm start",
         "unit": "ms/step", "higher_is_better": False, "dtype": "f32 sweeps, f64 pressure and norms",
         "plain": {"ms_per_step": mean("plain_ms"), "sor_iters_per_step": it_plain,
@@ -621,6 +628,7 @@ def run_les(args, rank, world, local, learned):
     torch.cuda.set_device(local)
     args.les_steps = args.steps
     args.les_spinup = args.spinup
+    args.les_horizon = max(args.les_horizon, args.steps)
     obj = les_object(args, local)
     if rank != 0:
         return
@@ -868,6 +876,8 @@ def main():
     ap.add_argument("--no-les", action="store_true", help="default workload: leave out the UFLES object")
     ap.add_argument("--les-spinup", type=int, default=20, help="UFLES object: spin-up steps before the comparison")
     ap.add_argument("--les-steps", type=int, default=10, help="UFLES object: compared states")
+    ap.add_argument("--les-horizon", type=int, default=180,
+                    help="UFLES object: steps after the spin-up over which the compared states are spread")
     ap.add_argument("--les-e2e-steps", type=int, default=3, help="UFLES object: steps per end-to-end timing")
     ap.add_argument("--check-every", type=int, default=500,
                     help="les workloads: SOR iterations between FP64 residual checks")

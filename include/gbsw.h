@@ -66,6 +66,24 @@ const char *gbsw_last_error(void);
  */
 gbsw_status gbsw_measure_l2_copy(long long bytes, int passes, double *gbs);
 
+/*
+ * Bounds-checked debug build (SURVEY-style sanitizer substitute; the paper
+ * has no counterpart).  libgbsw_debug.so, built from the same sources with
+ * GBSW_DEBUG_BOUNDS=1, tests every global index of the 2DSW kernels (the
+ * streaming, tile and ensemble kernels) and of the SOR sweep against its
+ * buffer's extent before the access; a failed test skips the access and
+ * is counted, so a wrong index never faults.  gbsw_debug_bounds writes the
+ * count since the last call to *violations (and clears it), returning
+ * GBSW_ERR_DEVICE_BOUNDS if it is not 0; in the product build it writes -1
+ * and returns GBSW_OK.  Synchronises the device.
+ */
+gbsw_status gbsw_debug_bounds(long long *violations);
+
+/* Self-test of that index test: checks index n of an n-element device
+ * buffer (no access is made) and returns GBSW_ERR_DEVICE_BOUNDS when the
+ * violation was counted, in either build.  Synchronous. */
+gbsw_status gbsw_selftest_bounds(void);
+
 /* Self-test of the bounded device-side waits (the paper has no
  * counterpart).  which = 0 waits on an mbarrier phase that never completes
  * for `budget` clock cycles, which = 1 spins on a flag that is never set
@@ -152,15 +170,18 @@ gbsw_status sw_set_state(gbsw_sw *sw, const float *eta, const float *u, const fl
 gbsw_status sw_set_blocking(gbsw_sw *sw, int steps_per_launch);
 
 /* Tiling of the fused kernel: steps per launch (0 = automatic, else 1..6)
- * and the row-segment height of a thread block (0 = automatic: one wave of
- * resident blocks, segments of at least 8T rows).  Results do not depend
- * on the tiling (every operation is rounded as written). */
+ * and the row-segment height of a thread block of the streaming kernel (0 =
+ * automatic: one wave of resident blocks, segments of at least 8T rows),
+ * or rows = -1 for the tile kernel (32 x 32 cells and a 2T-cell halo per
+ * block in shared memory, T = 1..3), made for grids that fit in L2.
+ * Results do not depend on the tiling (every operation is rounded as
+ * written). */
 gbsw_status sw_set_tiling(gbsw_sw *sw, int steps_per_launch, int rows);
 
 /* Choose the tiling by measurement: times trial_steps (1..100000, rounded
  * to whole launches) on the context's own state for each depth T = 1..6
  * and row-segment heights giving the default, one, two and three waves of
- * resident blocks, keeps the fastest (written to *T_out, *rows_out if
+ * resident blocks, and the tile kernel for T = 1..3, keeps the fastest (written to *T_out, *rows_out if
  * non-NULL) and restores the state exactly.  Allocates a copy of the state;
  * synchronous.  The paper's grids (Sec. 6.2: 500^2 to 2000^2) are small
  * enough to stay in L2, where the best tiling differs from the 4096^2
@@ -338,6 +359,24 @@ gbsw_status les_set_field(gbsw_les *les, int field, const void *host);
 gbsw_status les_get_step(gbsw_les *les, int *step);
 gbsw_status les_set_step(gbsw_les *les, int step);
 
+/* The whole state that the next step depends on (Sec. 6.3.1: the
+ * predicted velocity that velnw projects, the pressure, the previous
+ * tendencies of adam and the time integrals of feedbf), as host buffers in
+ * the padded layout above, plus the step count.  A NULL buffer is skipped. */
+typedef struct {
+    float *u, *v, *w;        /* u*, v*, w* */
+    double *p;               /* pressure (FP64) */
+    float *fu_old, *fv_old, *fw_old;
+    float *gu, *gv, *gw;
+    int step;
+} gbsw_les_state;
+
+/* Checkpoint and restart: copy the state out of / into the context.  The
+ * next step from a restored state is bitwise the step the context would
+ * have taken.  Synchronous. */
+gbsw_status les_get_state(gbsw_les *les, gbsw_les_state *state);
+gbsw_status les_set_state(gbsw_les *les, const gbsw_les_state *state);
+
 /* Change the SOR parameters of later steps. */
 gbsw_status les_set_solver(gbsw_les *les, double omega, double tol, int max_iter, int check_every);
 
@@ -470,6 +509,9 @@ gbsw_status unet_set_params(gbsw_unet *net, const float *host, int n);
  * planes).  Synchronous.
  */
 gbsw_status unet_forward(gbsw_unet *net, int n, int D, int H, int W, const float *x, float *y);
+
+/* The same forward pass under the name of the boundary's inference call. */
+gbsw_status unet_infer(gbsw_unet *net, int n, int D, int H, int W, const float *x, float *y);
 
 /* MSE loss against target (device, n*D*H*W FP32) and the parameter
  * gradients (host array of unet_num_params(), or NULL), no update. */

@@ -69,12 +69,17 @@ def _declare(L):
 
 
 def lib():
-    """Load libgbsw.so once; raise if it has not been built."""
+    """Load libgbsw.so once (libgbsw_debug.so, the bounds-checked build, when
+    the environment sets GBSW_DEBUG_BOUNDS=1); raise if it has not been
+    built."""
     global _lib
     if _lib is None:
-        if not os.path.exists(LIB_PATH):
-            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1711_04471_gb300.build.build()")
-        L = C.CDLL(LIB_PATH)
+        path = LIB_PATH
+        if os.environ.get("GBSW_DEBUG_BOUNDS") == "1":
+            path = os.path.join(os.path.dirname(LIB_PATH), "libgbsw_debug.so")
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with paper_1711_04471_gb300.build.build()")
+        L = C.CDLL(path)
         _declare(L)
         _lib = L
     return _lib

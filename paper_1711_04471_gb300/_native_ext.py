@@ -15,6 +15,11 @@ class LESStats(C.Structure):
                 ("ms_solve", C.c_float), ("ms_guess", C.c_float)]
 
 
+class LESState(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("u", "v", "w", "p", "fu_old", "fv_old", "fw_old", "gu", "gv", "gw")] + \
+               [("step", C.c_int)]
+
+
 def declare(L, sig):
     vp, ip, dp = C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_double)
     sig(L, "sw_volume_noalloc", C.c_int,
@@ -48,6 +53,9 @@ def declare(L, sig):
     sig(L, "unet_get_params", C.c_int, [vp, vp, C.c_int])
     sig(L, "unet_set_params", C.c_int, [vp, vp, C.c_int])
     sig(L, "unet_forward", C.c_int, [vp, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp])
+    sig(L, "unet_infer", C.c_int, [vp, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp])
+    sig(L, "les_get_state", C.c_int, [vp, C.POINTER(LESState)])
+    sig(L, "les_set_state", C.c_int, [vp, C.POINTER(LESState)])
     sig(L, "unet_gradients", C.c_int, [vp, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp, dp])
     sig(L, "unet_train_step", C.c_int, [vp, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, C.c_float, dp])
     sig(L, "unet_destroy", None, [vp])
@@ -57,6 +65,8 @@ def declare(L, sig):
     sig(L, "warm_start_apply", C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, vp, C.c_double, vp, vp])
     sig(L, "gbsw_selftest_wait", C.c_int, [C.c_int, C.c_longlong])
     sig(L, "gbsw_measure_l2_copy", C.c_int, [C.c_longlong, C.c_int, dp])
+    sig(L, "gbsw_debug_bounds", C.c_int, [C.POINTER(C.c_longlong)])
+    sig(L, "gbsw_selftest_bounds", C.c_int, [])
     sig(L, "gbsw_selftest_sor_division", C.c_int, [C.c_int, C.POINTER(C.c_ulonglong)])
     sig(L, "poisson_solve", C.c_int, [C.c_int, C.c_int, C.c_int, C.c_double, vp, vp, C.c_double, C.c_double,
                                       C.c_int, C.c_int, vp, ip, dp])

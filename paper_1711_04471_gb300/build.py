@@ -3,6 +3,8 @@
 Each translation unit under csrc/ is compiled in parallel with nvcc and the
 objects are linked into paper_1711_04471_gb300/libgbsw.so.  No cmake; a
 rebuild happens only when a source or header is newer than the library.
+build(debug=True) makes the bounds-checked variant libgbsw_debug.so from
+the same sources (GBSW_DEBUG_BOUNDS=1, objects in _build_debug/).
 """
 from __future__ import annotations
 
@@ -18,6 +20,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OBJDIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgbsw.so")
+OBJDIR_DEBUG = os.path.join(HERE, "_build_debug")
+LIB_DEBUG = os.path.join(HERE, "libgbsw_debug.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 
@@ -40,24 +44,32 @@ def sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib: str) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = glob.glob(os.path.join(CSRC, "*")) + glob.glob(os.path.join(ROOT, "include", "*.h")) + [__file__]
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and not _stale():
-        return LIB
-    os.makedirs(OBJDIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+    """Path of libgbsw.so (of libgbsw_debug.so with debug), compiled first
+    if a source is newer.  With GBSW_DEBUG_BOUNDS=1 in the environment the
+    product build also brings the debug library up to date (it is the one
+    the binding then loads)."""
+    if not debug and os.environ.get("GBSW_DEBUG_BOUNDS") == "1":
+        build(force, verbose, debug=True)
+    lib, objdir = (LIB_DEBUG, OBJDIR_DEBUG) if debug else (LIB, OBJDIR)
+    if not force and not _stale(lib):
+        return lib
+    os.makedirs(objdir, exist_ok=True)
     cc = nvcc()
     srcs = sources()
+    extra = ["-DGBSW_DEBUG_BOUNDS=1"] if debug else []
 
     def compile_one(src):
-        obj = os.path.join(OBJDIR, os.path.basename(src) + ".o")
-        cmd = [cc, *_flags(verbose), "-c", src, "-o", obj]
+        obj = os.path.join(objdir, os.path.basename(src) + ".o")
+        cmd = [cc, *_flags(verbose), *extra, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0 or verbose:
             sys.stderr.write(r.stdout + r.stderr)
@@ -67,12 +79,12 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         objs = list(ex.map(compile_one, srcs))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [cc, ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lcuda"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, debug="--debug" in sys.argv))

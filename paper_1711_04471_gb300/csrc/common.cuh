@@ -29,6 +29,35 @@ inline gbsw_status dev_status_to_gbsw(int s)
     }
 }
 
+// Bounds-checked debug build (compiled with -DGBSW_DEBUG_BOUNDS=1 into
+// libgbsw_debug.so): the 2DSW and SOR kernels test every global index
+// against the extent of its buffer before the access.  A failed test skips
+// the access (a load gives 0) and counts the violation in a device word of
+// its translation unit; gbsw_debug_bounds reads and clears the counts.
+// The product build compiles the tests away.
+#ifndef GBSW_DEBUG_BOUNDS
+#define GBSW_DEBUG_BOUNDS 0
+#endif
+
+__device__ __forceinline__ bool index_ok(long long i, long long n, unsigned *count)
+{
+    if (i >= 0 && i < n) return true;
+    atomicAdd(count, 1u);
+    return false;
+}
+
+#if GBSW_DEBUG_BOUNDS
+#define GBSW_INBOUNDS(i, n, count) ::gbsw::index_ok((long long)(i), (long long)(n), (count))
+#else
+#define GBSW_INBOUNDS(i, n, count) true
+#endif
+
+// Violation counts of the debug build, read and cleared (one function per
+// translation unit that has checked kernels; 0 in the product build).
+unsigned long long take_bounds_sw();
+unsigned long long take_bounds_batch();
+unsigned long long take_bounds_poisson();
+
 // Remember the last CUDA error text for diagnostics.
 void record_cuda_error(cudaError_t e, const char *what, const char *file, int line);
 

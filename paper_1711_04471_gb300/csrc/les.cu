@@ -587,6 +587,32 @@ gbsw_status les_set_field(gbsw_les *s, int field, const void *host)
     return GBSW_OK;
 }
 
+gbsw_status les_get_state(gbsw_les *s, gbsw_les_state *st)
+{
+    if (!s || !st) return GBSW_ERR_ARG;
+    void *bufs[10] = {st->u, st->v, st->w, st->p, st->fu_old, st->fv_old, st->fw_old, st->gu, st->gv, st->gw};
+    for (int f = 0; f < 10; ++f)
+        if (bufs[f]) {
+            gbsw_status r = les_get_field(s, f, bufs[f]);
+            if (r != GBSW_OK) return r;
+        }
+    st->step = s->step;
+    return GBSW_OK;
+}
+
+gbsw_status les_set_state(gbsw_les *s, const gbsw_les_state *st)
+{
+    if (!s || !st || st->step < 0) return GBSW_ERR_ARG;
+    const void *bufs[10] = {st->u, st->v, st->w, st->p, st->fu_old, st->fv_old, st->fw_old, st->gu, st->gv, st->gw};
+    for (int f = 0; f < 10; ++f)
+        if (bufs[f]) {
+            gbsw_status r = les_set_field(s, f, bufs[f]);
+            if (r != GBSW_OK) return r;
+        }
+    s->step = st->step;
+    return GBSW_OK;
+}
+
 gbsw_status les_get_step(gbsw_les *s, int *step)
 {
     if (!s || !step) return GBSW_ERR_ARG;

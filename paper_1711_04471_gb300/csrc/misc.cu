@@ -57,3 +57,17 @@ const char *gbsw_last_error(void) { return gbsw::g_last_error; }
 int gbsw_version(void) { return 100; }
 
 }  // extern "C"
+
+// Out-of-range index counts of the bounds-checked debug build.
+extern "C" gbsw_status gbsw_debug_bounds(long long *violations)
+{
+    if (!violations) return GBSW_ERR_ARG;
+    if (!GBSW_DEBUG_BOUNDS) {
+        *violations = -1;  // the product build has no checks
+        return GBSW_OK;
+    }
+    GBSW_CUDA_TRY(cudaDeviceSynchronize());
+    const unsigned long long n = gbsw::take_bounds_sw() + gbsw::take_bounds_batch() + gbsw::take_bounds_poisson();
+    *violations = (long long)n;
+    return n ? GBSW_ERR_DEVICE_BOUNDS : GBSW_OK;
+}

@@ -18,6 +18,17 @@
 
 namespace gbsw {
 
+// Out-of-range index count of the bounds-checked debug build.
+static __device__ unsigned g_sor_bounds;
+
+unsigned long long take_bounds_poisson()
+{
+    unsigned h = 0, zero = 0;
+    if (cudaMemcpyFromSymbol(&h, g_sor_bounds, sizeof(h)) != cudaSuccess) return 0;
+    cudaMemcpyToSymbol(g_sor_bounds, &zero, sizeof(zero));
+    return h;
+}
+
 __device__ __forceinline__ long long pidx(const PDims &d, int i, int j, int k)
 {
     return (long long)k * d.plane + (long long)j * d.pitch + i;
@@ -83,6 +94,12 @@ sor_sweep_kernel(PDims d, int colour, float omega, float h2, SorDiag dg, float *
     const int o = j * d.cpitch + SOR_SLOT0 + s0;  // offset inside a colour plane
     const int oym = o + (jm - j) * d.cpitch, oyp = o + (jp - j) * d.cpitch;
     const int cpl = (int)d.cplane;
+#if GBSW_DEBUG_BOUNDS
+    const long long nc = (long long)d.cplane * (d.nz + 2);  // elements of each colour array
+#endif
+#define SOR_OK4(idx) GBSW_INBOUNDS((long long)(idx), nc - 3, &g_sor_bounds)
+#define SOR_OK1(idx) GBSW_INBOUNDS((long long)(idx), nc, &g_sor_bounds)
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
     for (int h = 0; h < SOR_KZ; ++h) {
         const int k = SOR_KZ * blockIdx.z + 1 + h;
@@ -96,26 +113,26 @@ sor_sweep_kernel(PDims d, int colour, float omega, float h2, SorDiag dg, float *
         const float d_in = mid ? dg.d[2] : dg.d[1], y_in = mid ? dg.y[2] : dg.y[1];
         const float d_lo = mid ? dg.d[1] : dg.d[0], y_lo = mid ? dg.y[1] : dg.y[0];
         const float d_hi = mid ? dg.d[3] : dg.d[2], y_hi = mid ? dg.y[3] : dg.y[2];
-        const float4 e_old = FIRST ? make_float4(0.f, 0.f, 0.f, 0.f) : *reinterpret_cast<const float4 *>(ep + o);
-        const float4 r4 = *reinterpret_cast<const float4 *>(rc + plane + o);
+        const float4 e_old = (FIRST || !SOR_OK4(plane + o)) ? zero4 : *reinterpret_cast<const float4 *>(ep + o);
+        const float4 r4 = SOR_OK4(plane + o) ? *reinterpret_cast<const float4 *>(rc + plane + o) : zero4;
         float sx[4] = {0.f, 0.f, 0.f, 0.f}, sy[4] = {0.f, 0.f, 0.f, 0.f}, sz[4] = {0.f, 0.f, 0.f, 0.f};
         if (need_nb) {
-            const float4 oc = *reinterpret_cast<const float4 *>(op + o);
-            const float4 zm = *reinterpret_cast<const float4 *>(op + o - cpl);
-            const float4 zp = *reinterpret_cast<const float4 *>(op + o + cpl);
-            const float4 ym = *reinterpret_cast<const float4 *>(op + oym);
-            const float4 yp = *reinterpret_cast<const float4 *>(op + oyp);
+            const float4 oc = SOR_OK4(plane + o) ? *reinterpret_cast<const float4 *>(op + o) : zero4;
+            const float4 zm = SOR_OK4(plane + o - cpl) ? *reinterpret_cast<const float4 *>(op + o - cpl) : zero4;
+            const float4 zp = SOR_OK4(plane + o + cpl) ? *reinterpret_cast<const float4 *>(op + o + cpl) : zero4;
+            const float4 ym = SOR_OK4(plane + oym) ? *reinterpret_cast<const float4 *>(op + oym) : zero4;
+            const float4 yp = SOR_OK4(plane + oyp) ? *reinterpret_cast<const float4 *>(op + oyp) : zero4;
             // x neighbours of slot s are slots s - 1 + q and s + q of the other colour
             if (FLAT) {
-                const float xe = op[o + (q ? 4 : -1)];
+                const float xe = SOR_OK1(plane + o + (q ? 4 : -1)) ? op[o + (q ? 4 : -1)] : 0.0f;
                 const float w[6] = {xe, oc.x, oc.y, oc.z, oc.w, xe};
 #pragma unroll
                 for (int u = 0; u < 4; ++u) sx[u] = q ? w[u + 1] + w[u + 2] : w[u] + w[u + 1];
             } else if (q == 0) {
-                const float ol = op[o - 1];
+                const float ol = SOR_OK1(plane + o - 1) ? op[o - 1] : 0.0f;
                 sx[0] = ol + oc.x; sx[1] = oc.x + oc.y; sx[2] = oc.y + oc.z; sx[3] = oc.z + oc.w;
             } else {
-                const float orr = op[o + 4];
+                const float orr = SOR_OK1(plane + o + 4) ? op[o + 4] : 0.0f;
                 sx[0] = oc.x + oc.y; sx[1] = oc.y + oc.z; sx[2] = oc.z + oc.w; sx[3] = oc.w + orr;
             }
             sy[0] = ym.x + yp.x; sy[1] = ym.y + yp.y; sy[2] = ym.z + yp.z; sy[3] = ym.w + yp.w;
@@ -132,8 +149,10 @@ sor_sweep_kernel(PDims d, int colour, float omega, float h2, SorDiag dg, float *
             const float yc = i == 1 ? y_lo : (i == d.nx ? y_hi : y_in);
             u[tt] = i <= d.nx ? eo4[tt] + omega * (sor_div(s - h2 * rr4[tt], dc, yc) - eo4[tt]) : 0.0f;
         }
-        *reinterpret_cast<float4 *>(ep + o) = make_float4(u[0], u[1], u[2], u[3]);
+        if (SOR_OK4(plane + o)) *reinterpret_cast<float4 *>(ep + o) = make_float4(u[0], u[1], u[2], u[3]);
     }
+#undef SOR_OK4
+#undef SOR_OK1
 }
 
 // r = b - A p_hi in FP64 (the correction has been folded into p_hi; r is

@@ -7,6 +7,8 @@
 // (sor_div) against the IEEE division x / d for every finite FP32 x.
 // gbsw_measure_l2_copy: the copy bandwidth of buffers that stay in L2, the
 // ceiling of a kernel whose working set stays in L2 between passes.
+// gbsw_selftest_bounds: the index test of the bounds-checked debug build,
+// given an index one past the end of a buffer (no access is made).
 #include "common.cuh"
 #include "poisson.cuh"
 #include "tc.cuh"
@@ -69,7 +71,33 @@ __global__ void __launch_bounds__(512) l2_copy_kernel(const float4 *__restrict__
         for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += stride) dst[q] = src[q];
 }
 
+// The debug build's index test on index n of an n-element buffer: the
+// test fails, counts the violation, and the access it guards is skipped.
+__global__ void selftest_bounds_kernel(const float *buf, long long n, unsigned *count, float *out)
+{
+    if (threadIdx.x == 0) *out = gbsw::index_ok(n, n, count) ? buf[n] : 0.0f;
+}
+
 }  // namespace
+
+extern "C" gbsw_status gbsw_selftest_bounds(void)
+{
+    unsigned *d = nullptr;  // [0] count, [1..] the guarded buffer and the result
+    GBSW_CUDA_TRY(cudaMalloc((void **)&d, 8 * sizeof(unsigned)));
+    unsigned h = 0;
+    cudaError_t e = cudaMemset(d, 0, 8 * sizeof(unsigned));
+    if (e == cudaSuccess) {
+        selftest_bounds_kernel<<<1, 32>>>((const float *)(d + 1), 4, d, (float *)(d + 6));
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof(h), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) {
+        gbsw::record_cuda_error(e, "gbsw_selftest_bounds", __FILE__, __LINE__);
+        return GBSW_ERR_CUDA;
+    }
+    return h == 1 ? GBSW_ERR_DEVICE_BOUNDS : GBSW_ERR_CUDA;
+}
 
 extern "C" gbsw_status gbsw_measure_l2_copy(long long bytes, int passes, double *gbs)
 {

@@ -14,6 +14,7 @@
 #include "common.cuh"
 #include "sw_kernels.cuh"
 #include "sw_stream.cuh"
+#include "sw_tile.cuh"
 
 using namespace gbsw;
 
@@ -156,12 +157,32 @@ cudaError_t launch_stream(const gbsw_sw *s, int rows, cudaStream_t st, const flo
     return cudaGetLastError();
 }
 
-// One launch of depth T from buffer set a into the other one, on stream st.
+// One launch of the tile kernel of depth T (1..SWT_MAX_T).
+template <int T>
+cudaError_t launch_tile(const gbsw_sw *s, cudaStream_t st, const float *eta_in, const float *u_in, const float *v_in,
+                        float *eta_out, float *u_out, float *v_out)
+{
+    const dim3 grid(ceil_div(s->d.nx, SWT_W), ceil_div(s->d.ny, SWT_H));
+    sw_tile_kernel<T><<<grid, SWT_THREADS, 0, st>>>(s->d, s->H, eta_in, u_in, v_in, eta_out, u_out, v_out);
+    return cudaGetLastError();
+}
+
+// One launch of depth T from buffer set a into the other one, on stream st:
+// rows > 0 the streaming kernel over row segments of that height, rows < 0
+// the tile kernel.
 cudaError_t launch_from(const gbsw_sw *s, int T, int rows, int a, cudaStream_t st)
 {
     const int b = 1 - a;
     const float *ei = s->eta[a], *ui = s->u[a], *vi = s->v[a];
     float *eo = s->eta[b], *uo = s->u[b], *vo = s->v[b];
+    if (rows < 0) {
+        switch (T) {
+        case 1: return launch_tile<1>(s, st, ei, ui, vi, eo, uo, vo);
+        case 2: return launch_tile<2>(s, st, ei, ui, vi, eo, uo, vo);
+        case 3: return launch_tile<3>(s, st, ei, ui, vi, eo, uo, vo);
+        default: return cudaErrorInvalidValue;
+        }
+    }
     switch (T) {
     case 1: return launch_stream<1>(s, rows, st, ei, ui, vi, eo, uo, vo);
     case 2: return launch_stream<2>(s, rows, st, ei, ui, vi, eo, uo, vo);
@@ -177,7 +198,7 @@ int auto_blocking(const gbsw_sw *) { return 3; }
 
 int tiling_T(const gbsw_sw *s) { return s->blocking > 0 ? s->blocking : auto_blocking(s); }
 
-int tiling_rows(const gbsw_sw *s, int T) { return s->rows > 0 ? s->rows : default_rows(s, T); }
+int tiling_rows(const gbsw_sw *s, int T) { return s->rows != 0 ? s->rows : default_rows(s, T); }
 
 void drop_chunks(gbsw_sw *s)
 {
@@ -240,7 +261,7 @@ gbsw_status run_steps(gbsw_sw *s, int nsteps, int T, int rows)
     }
     for (int k = 0; k < full + (rest > 0); ++k) {
         const int t = k < full ? T : rest;
-        cudaError_t e = launch_from(s, t, t == T ? rows : default_rows(s, t), s->cur, s->stream);
+        cudaError_t e = launch_from(s, t, (t == T || rows < 0) ? rows : default_rows(s, t), s->cur, s->stream);
         if (e != cudaSuccess) {
             record_cuda_error(e, "sw_stream_kernel", __FILE__, __LINE__);
             return GBSW_ERR_CUDA;
@@ -344,7 +365,8 @@ gbsw_status sw_set_blocking(gbsw_sw *s, int steps_per_launch)
 
 gbsw_status sw_set_tiling(gbsw_sw *s, int steps_per_launch, int rows)
 {
-    if (!s || steps_per_launch < 0 || steps_per_launch > SW_MAX_BLOCKING || rows < 0) return GBSW_ERR_ARG;
+    if (!s || steps_per_launch < 0 || steps_per_launch > SW_MAX_BLOCKING || rows < -1) return GBSW_ERR_ARG;
+    if (rows == -1 && (steps_per_launch < 1 || steps_per_launch > SWT_MAX_T)) return GBSW_ERR_ARG;
     s->blocking = steps_per_launch;
     s->rows = rows;
     return GBSW_OK;
@@ -387,10 +409,11 @@ gbsw_status sw_autotune(gbsw_sw *s, int trial_steps, int *T_out, int *rows_out)
             // segment heights: the default, and those giving 1, 2, 3 waves of resident CTAs
             const int strips = ceil_div(s->d.nx, SWS_THREADS - 4 * T);
             const int capacity = stream_per_sm(T) * sm_count();
-            int cand[4] = {default_rows(s, T), 0, 0, 0};
+            int cand[5] = {default_rows(s, T), 0, 0, 0, T <= SWT_MAX_T ? -1 : 0};  // -1: the tile kernel
             for (int w = 1; w <= 3; ++w)
                 cand[w] = std::max(2, ceil_div(s->d.ny, std::max(1, ceil_div(w * capacity, strips))));
-            for (int c = 0; c < 4 && st == GBSW_OK; ++c) {
+            for (int c = 0; c < 5 && st == GBSW_OK; ++c) {
+                if (cand[c] == 0) continue;
                 bool seen = false;
                 for (int q = 0; q < c; ++q) seen |= cand[q] == cand[c];
                 if (seen) continue;
@@ -622,3 +645,13 @@ extern "C" gbsw_status sw_volume_noalloc(int nx, int ny, int pitch, double dx, d
     GBSW_LAUNCH_CHECK();
     return GBSW_OK;
 }
+
+namespace gbsw {
+unsigned long long take_bounds_sw()
+{
+    unsigned h = 0, zero = 0;
+    if (cudaMemcpyFromSymbol(&h, g_sw_bounds, sizeof(h)) != cudaSuccess) return 0;
+    cudaMemcpyToSymbol(g_sw_bounds, &zero, sizeof(zero));
+    return h;
+}
+}  // namespace gbsw

@@ -662,3 +662,13 @@ void sw_batch_destroy(gbsw_sw_batch *b)
 }
 
 }  // extern "C"
+
+namespace gbsw {
+unsigned long long take_bounds_batch()
+{
+    unsigned h = 0, zero = 0;
+    if (cudaMemcpyFromSymbol(&h, g_sw_bounds, sizeof(h)) != cudaSuccess) return 0;
+    cudaMemcpyToSymbol(g_sw_bounds, &zero, sizeof(zero));
+    return h;
+}
+}  // namespace gbsw

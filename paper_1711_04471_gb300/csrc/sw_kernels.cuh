@@ -27,6 +27,10 @@ constexpr int SW_VOL_BLOCKS = 1024;  // fixed, so the FP64 sum order is fixed
 constexpr int SW_VOL_THREADS = 256;
 constexpr int SW_NOALLOC_MAX_SIDE = 1 << 20;  // largest nx, ny accepted by sw_volume_noalloc
 
+// Out-of-range index count of the bounds-checked debug build (one per
+// translation unit that includes this header).
+static __device__ unsigned g_sw_bounds;
+
 // Wet/dry face rule: keep the predicted velocity if both cells are wet, or
 // if it flows out of a wet cell; otherwise the face is closed.
 __device__ __forceinline__ float sw_face_mask(float vel, bool wet_behind, bool wet_ahead)

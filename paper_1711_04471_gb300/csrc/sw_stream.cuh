@@ -111,9 +111,10 @@ __device__ __forceinline__ void sw_stream_tile(const SWDev &p, int strip, int r0
         mail[t] = SWRow{0, 0, 0, 0};
     }
 
+    const long long extent = (long long)p.ny * p.pitch;  // elements of each field of this grid
     auto load_row = [&](int n) {
         SWRow r{0.0f, 0.0f, 0.0f, 0.0f};
-        if (col_in && n >= 0 && n < p.ny) {
+        if (col_in && n >= 0 && n < p.ny && GBSW_INBOUNDS((long long)n * p.pitch + gi, extent, &g_sw_bounds)) {
             const size_t g = (size_t)n * p.pitch + gi;
             r.eta = sw_load<LP>(eta_in + g);
             r.u = sw_load<LP>(u_in + g);
@@ -224,7 +225,8 @@ __device__ __forceinline__ void sw_stream_tile(const SWDev &p, int strip, int r0
         }
         // the last stage's row is final: level T at row n - 3T + 1
         const int out_row = n - 3 * T + 1;
-        if (owned && out_row >= r0 && out_row < r1) {
+        if (owned && out_row >= r0 && out_row < r1 &&
+            GBSW_INBOUNDS((long long)out_row * p.pitch + gi, extent, &g_sw_bounds)) {
             const size_t g = (size_t)out_row * p.pitch + gi;
             eta_out[g] = mail[T - 1].eta;
             u_out[g] = mail[T - 1].u;

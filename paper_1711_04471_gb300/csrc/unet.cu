@@ -458,6 +458,11 @@ gbsw_status unet_forward(gbsw_unet *u, int n, int D, int H, int W, const float *
     return check_status(u);
 }
 
+gbsw_status unet_infer(gbsw_unet *u, int n, int D, int H, int W, const float *x, float *y)
+{
+    return unet_forward(u, n, D, H, W, x, y);
+}
+
 // Loss and gradients (no update); grads_host may be NULL.
 gbsw_status unet_gradients(gbsw_unet *u, int n, int D, int H, int W, const float *x, const float *target,
                            float *grads_host, double *loss)

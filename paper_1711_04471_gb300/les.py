@@ -8,7 +8,7 @@ import ctypes as C
 import numpy as np
 
 from . import _native as N
-from ._native_ext import LESParams, LESStats
+from ._native_ext import LESParams, LESState, LESStats
 
 FIELDS = dict(u=0, v=1, w=2, p=3, fuo=4, fvo=5, fwo=6, gu=7, gv=8, gw=9, nut=10, b=11)
 
@@ -53,6 +53,34 @@ class LES:
         if a.shape != (nz + 2, ny + 2, nx + 2):
             raise ValueError("fields are exchanged in the padded (nz+2, ny+2, nx+2) layout")
         N.check(N.lib().les_set_field(self._h, FIELDS[name], a.ctypes.data_as(C.c_void_p)), "les_set_field")
+
+    STATE = ("u", "v", "w", "p", "fu_old", "fv_old", "fw_old", "gu", "gv", "gw")
+
+    def get_state(self) -> dict:
+        """Checkpoint: every field the next step depends on (padded layout)
+        and the step count."""
+        nz, ny, nx = self.shape
+        out = {n: np.empty((nz + 2, ny + 2, nx + 2), dtype=np.float64 if n == "p" else np.float32)
+               for n in self.STATE}
+        st = LESState(*[out[n].ctypes.data for n in self.STATE], 0)
+        N.check(N.lib().les_get_state(self._h, C.byref(st)), "les_get_state")
+        out["step"] = st.step
+        return out
+
+    def set_state(self, state: dict):
+        """Restart from a checkpoint of get_state (fields missing from the
+        dict keep their current values)."""
+        nz, ny, nx = self.shape
+        keep = {}
+        for n in self.STATE:
+            if n in state:
+                a = np.ascontiguousarray(state[n], dtype=np.float64 if n == "p" else np.float32)
+                if a.shape != (nz + 2, ny + 2, nx + 2):
+                    raise ValueError("fields are exchanged in the padded (nz+2, ny+2, nx+2) layout")
+                keep[n] = a
+        st = LESState(*[keep[n].ctypes.data if n in keep else None for n in self.STATE],
+                      int(state.get("step", self.step_count)))
+        N.check(N.lib().les_set_state(self._h, C.byref(st)), "les_set_state")
 
     @property
     def step_count(self) -> int:

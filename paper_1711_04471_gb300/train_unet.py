@@ -3,11 +3,11 @@ solver, and compare the learned warm start with the plain one.
 
 Training data (the recipe of the learned warm start): LES runs on the
 256 x 256 x 128 workload grid (dx = 4 m, 20 % building cover) with other
-building seeds than the evaluation run: the 32 steps after the first 17
-(the stage of the run that is evaluated; the first steps, dominated by the
-start-up transient, are solved to a looser tolerance and not used).  From each step the plain solve's
-previous pressure p_prev, right-hand side b and converged pressure p
-(relative residual 1e-6) give one pair on the grid coarsened by f:
+building seeds than the evaluation runs, over the stage of the run that is
+evaluated (steps 2-201; --start steps before the first pair, of which all
+but the last are solved to a looser tolerance).  From each step the
+solve's previous pressure p_prev, right-hand side b and converged pressure
+p (relative residual 1e-6) give one pair on the grid coarsened by f:
 
     input   warm_start_features(p_prev, b)            (coarse residual and pressure)
     target  block mean of (p - p_prev) / s             (s from the same call)
@@ -21,13 +21,19 @@ coarse tensors by augment), and any linear combination of pairs is a pair
 Everything runs through the C ABI (les_*, warm_start_*, unet_*); the samples
 stay in device memory.
 
-The committed weights come from 13 runs (5 with base seed 3000, 8 with base
-seed 2000; the last one held out), generated and saved separately and then
-trained on together:
+The committed weights come from 28 runs of base seed 5000 (k = 0..27; the
+last one held out for validation), each 200 solved steps after one solved
+start-up step: 5,400 training pairs, 172,800 with the shifted and mirrored
+copies.  The runs used the previously committed weights (trained on 13
+shorter runs) as their warm start, which only shortens the solves: every
+target is the solver's pressure at the 1e-6 residual.  Generated in four
+calls (the pairs of 8 runs are about 37 MB) and trained on together:
 
-    python -m paper_1711_04471_gb300.train_unet --seeds 5 --base-seed 3000 --iters 0 --out x.npy --save-data b.npz
-    python -m paper_1711_04471_gb300.train_unet --seeds 8 --base-seed 2000 --iters 0 --out x.npy --save-data a.npz
-    python -m paper_1711_04471_gb300.train_unet --data b.npz a.npz --out weights.npy
+    python -m paper_1711_04471_gb300.train_unet --seeds 4 --first-seed 0 --base-seed 5000 --steps 200 --start 1 \
+        --iters 0 --out /tmp/x.npy --save-data gen_5000_0.npz --gen-weights previous_weights.npy
+    (likewise --seeds 8 --first-seed 4, 12 and 20 into gen_5000_4/12/20.npz)
+    python -m paper_1711_04471_gb300.train_unet --data gen_5000_0.npz gen_5000_4.npz gen_5000_12.npz gen_5000_20.npz \
+        --iters 100000 --out weights.npy
 """
 from __future__ import annotations
 
@@ -97,12 +103,15 @@ def mixed_batch(X, T, S, idx_a, idx_b, gen):
 
 
 def generate(nseeds=8, steps=32, start=17, shape=(256, 256, 128), dx=4.0, f=16, base_seed=2000, spinup_tol=1e-4,
-             log=print):
+             log=print, first_seed=0, net=None):
     """Per-seed (X, T, S) CUDA tensors of the solved steps, X (n, D/f, H/f,
-    W/f, 2), T (n, D/f, H/f, W/f), S (n,) FP32 scales.  The first start - 1
-    steps solve to spinup_tol (they only bring the flow to the stage that
-    is evaluated), the next one to 1e-6 so that p_prev of the first pair is
-    a converged pressure."""
+    W/f, 2), T (n, D/f, H/f, W/f), S (n,) FP32 scales, for the building
+    seeds derive_seed(base_seed, k), k = first_seed .. first_seed + nseeds - 1.
+    The first start - 1 steps solve to spinup_tol (they only bring the flow
+    to the stage that is evaluated), the next one to 1e-6 so that p_prev of
+    the first pair is a converged pressure.  With net, the runs use it as
+    their warm start: the solves reach the same 1e-6 residual sooner, and
+    the target is still the solver's converged pressure."""
     import torch
 
     from . import inputs
@@ -111,10 +120,12 @@ def generate(nseeds=8, steps=32, start=17, shape=(256, 256, 128), dx=4.0, f=16, 
     out = []
     t0 = time.time()
     iters = []
-    for sd in range(nseeds):
+    for sd in range(first_seed, first_seed + nseeds):
         solid = inputs.les_buildings(nx, ny, nz, dx=dx, seed=inputs.derive_seed(base_seed, sd))
         X, T, S = [], [], []
         with LES(nx, ny, nz, solid, dx=dx, check_every=50, max_iter=200000) as les:
+            if net is not None:
+                les.set_warm_start(net)
             if start > 1:
                 les.set_solver(tol=spinup_tol)
                 les.step(start - 1, stats=False)
@@ -196,7 +207,6 @@ def compare_warm_starts(net, shape=(256, 256, 128), seed=1003, spinup=20, steps=
     from .les import LES
     nx, ny, nz = shape
     solid = inputs.les_buildings(nx, ny, nz, dx=4.0, seed=seed)
-    names = ("u", "v", "w", "p", "fuo", "fvo", "fwo", "gu", "gv", "gw")
     rows = []
     with LES(nx, ny, nz, solid, **les_kw) as ref, LES(nx, ny, nz, solid, **les_kw) as trial:
         if spinup_tol is not None and spinup > 1:
@@ -209,11 +219,9 @@ def compare_warm_starts(net, shape=(256, 256, 128), seed=1003, spinup=20, steps=
             ref.step(spinup, stats=False)
         trial.set_warm_start(net)
         for k in range(steps):
-            state = {n: ref.get(n) for n in names}
-            count = ref.step_count
-            for n in names:
-                trial.set(n, state[n])
-            trial.step_count = count
+            state = ref.get_state()
+            count = state["step"]
+            trial.set_state(state)
             a = ref.step(1)[0]
             b = trial.step(1)[0]
             rows.append(dict(plain_iters=a["iters"], nn_iters=b["iters"],
@@ -236,6 +244,8 @@ def main():
                                                "run of the last file is held out) instead of running the LES")
     ap.add_argument("--base-seed", type=int, default=2000, help="building seeds of the generated runs: "
                                                                  "derive_seed(base, k)")
+    ap.add_argument("--first-seed", type=int, default=0, help="first k of the generated runs")
+    ap.add_argument("--gen-weights", help="network weights used as the warm start while generating the runs")
     ap.add_argument("--save-data", help="write the solved pairs to this .npz")
     ap.add_argument("--iters", type=int, default=60000)
     ap.add_argument("--batch", type=int, default=32)
@@ -254,12 +264,21 @@ def main():
             z = np.load(path)
             data += [tuple(torch.from_numpy(z[f"{a}{k}"]).cuda() for a in "xts") for k in range(int(z["nseeds"]))]
     else:
-        data = generate(args.seeds, args.steps, start=args.start, f=args.factor, base_seed=args.base_seed)
+        gen_net = None
+        if args.gen_weights:
+            gen_net = UNet(seed=0)
+            gen_net.set_params(np.load(args.gen_weights))
+        data = generate(args.seeds, args.steps, start=args.start, f=args.factor, base_seed=args.base_seed,
+                        first_seed=args.first_seed, net=gen_net)
+        if gen_net is not None:
+            gen_net.close()
     if args.save_data:
         arrs = {"nseeds": np.array(len(data))}
         for k, (x, t, s) in enumerate(data):
             arrs[f"x{k}"], arrs[f"t{k}"], arrs[f"s{k}"] = x.cpu().numpy(), t.cpu().numpy(), s.cpu().numpy()
         np.savez_compressed(args.save_data, **arrs)
+        if args.iters == 0:
+            return
     Xtr, Ttr, Str = augment(torch.cat([d[0] for d in data[:-1]]), torch.cat([d[1] for d in data[:-1]]),
                             torch.cat([d[2] for d in data[:-1]]))
     Xval, Tval, _ = data[-1]
