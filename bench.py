@@ -53,10 +53,10 @@ CSRC = os.path.join(ROOT, "paper_1711_04471_gb300", "csrc")
 # bench then reports traffic as null until the kernel is captured again.
 NCU_TRAFFIC = {
     # one sw_stream_kernel<3> launch on the 4096^2 grid
-    "sw_stream_kernel<3>": (458.705664e6, ("sw_stream.cuh", "sw_kernels.cuh"), "a2f5ba752ad5f879"),
+    "sw_stream_kernel<3>": ((297.057536 + 163.139072) * 1e6, ("sw_stream.cuh", "sw_kernels.cuh"), "fdc57507af7e9c15"),
     # one SOR iteration (red + black half-sweep) on 256x256x128, L2 warm
-    "sor_iteration_256x256x128": ((1.734144 + 0.464896 + 2.585344 + 0.501504) * 1e6, ("poisson.cu", "poisson.cuh"),
-                                  "52501699356f9faa"),
+    "sor_iteration_256x256x128": ((1.893376 + 0.539392 + 2.571520 + 0.704768) * 1e6, ("poisson.cu", "poisson.cuh"),
+                                  "4687857857f775a0"),
 }
 
 
@@ -509,7 +509,10 @@ def les_compare(args, solid, shape=LES_SHAPE, log=lambda *a: None):
     that step from the same state, to the same tolerance (device times from
     the step's own CUDA events).  Both solves reach the same 1e-6 residual,
     so the run's states are those of a previous-pressure run to within the
-    solver tolerance.  Then each context continues for args.les_e2e_steps
+    solver tolerance.  The compared steps are the middle ones of `compared`
+    equal blocks of the horizon (a stratified sample: the first steps, the
+    most expensive, are represented like the rest).  Then each context
+    continues for args.les_e2e_steps
     steps timed end to end on the host: les_step plus the read-back of the
     FP64 pressure to host memory."""
     import numpy as np
@@ -525,7 +528,7 @@ def les_compare(args, solid, shape=LES_SHAPE, log=lambda *a: None):
         run.set_warm_start(net)
         run.step(args.les_spinup, stats=False)
         for k in range(1, horizon + 1):
-            if k % stride == 0 and len(rows) < compared:
+            if (k - 1) % stride == stride // 2 and len(rows) < compared:   # the middle step of each block
                 state = run.get_state()          # the same state for both warm starts
                 plain.set_state(state)
                 a = plain.step(1)[0]

@@ -4,9 +4,12 @@
 // A CTA loads a tile of SWT_W x SWT_H cells plus a halo of 2T cells on
 // every side (the dependency radius of one step is 2 cells) into shared
 // memory, advances the whole tile T steps there, and writes back the
-// middle SWT_W x SWT_H cells.  Each step is four barrier-separated phases
-// over the tile: depth h, momentum predictor u', v' (in place of u, v),
-// continuity eta*, masked Shapiro filter (in place of eta).  Cells past a
+// middle SWT_W x SWT_H cells.  Each step is three barrier-separated
+// phases over the tile: momentum predictor u', v'; continuity eta*;
+// masked Shapiro filter, which also forms the next step's depth h (in the
+// other of two h buffers, since this phase still reads the current one).
+// A thread keeps its own cells' values in registers (H never leaves
+// them); shared memory holds only what the neighbours read.  Cells past a
 // tile edge are not read (the results there are discarded halo); cells
 // outside the grid are loaded as H = eta = u = v = 0 and stay so, exactly
 // as in the streaming kernel.  Every operation is the streaming kernel's,
@@ -34,14 +37,24 @@ sw_tile_kernel(SWDev p, const float *__restrict__ H, const float *__restrict__ e
 {
     constexpr int HALO = 2 * T;
     constexpr int LW = SWT_W + 2 * HALO, LH = SWT_H + 2 * HALO, NC = LW * LH;
-    __shared__ float e[NC], uu[NC], vv[NC], HH[NC], hh[NC], es[NC];
+    constexpr int PER = (NC + SWT_THREADS - 1) / SWT_THREADS;  // cells per thread (2 for T <= 3)
+    // neighbours' values only: each thread keeps its own cells' values in registers
+    __shared__ float e[NC], uu[NC], vv[NC], hh2[2][NC], es[NC];  // depth double-buffered by step
     const int x0 = blockIdx.x * SWT_W - HALO, y0 = blockIdx.y * SWT_H - HALO;
     const float hmin = p.hmin;
 
-    for (int q = threadIdx.x; q < NC; q += SWT_THREADS) {
-        const int lx = q % LW, ly = q / LW, gx = x0 + lx, gy = y0 + ly;
+    float re[PER], ru[PER], rv[PER], rH[PER], rh[PER], rs[PER];
+    int lx[PER], ly[PER];
+    bool act[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int q = threadIdx.x + k * SWT_THREADS;
+        act[k] = q < NC;
+        lx[k] = q % LW;
+        ly[k] = q / LW;
+        const int gx = x0 + lx[k], gy = y0 + ly[k];
         float a = 0.0f, b = 0.0f, c = 0.0f, d = 0.0f;
-        if (gx >= 0 && gx < p.nx && gy >= 0 && gy < p.ny &&
+        if (act[k] && gx >= 0 && gx < p.nx && gy >= 0 && gy < p.ny &&
             GBSW_INBOUNDS((long long)gy * p.pitch + gx, (long long)p.ny * p.pitch, &g_sw_bounds)) {
             const size_t g = (size_t)gy * p.pitch + gx;
             a = __ldg(eta_in + g);
@@ -49,49 +62,70 @@ sw_tile_kernel(SWDev p, const float *__restrict__ H, const float *__restrict__ e
             c = __ldg(v_in + g);
             d = __ldg(H + g);
         }
-        e[q] = a;
-        uu[q] = b;
-        vv[q] = c;
-        HH[q] = d;
+        re[k] = a;
+        ru[k] = b;
+        rv[k] = c;
+        rH[k] = d;
+        rs[k] = 0.0f;
+        // depth of the first step, and the fields the neighbours read
+        rh[k] = __fadd_rn(rH[k], re[k]);
+        if (act[k]) {
+            hh2[0][threadIdx.x + k * SWT_THREADS] = rh[k];
+            e[threadIdx.x + k * SWT_THREADS] = re[k];
+        }
     }
     __syncthreads();
-#pragma unroll 1
+    // The step loop is unrolled so that each step's pair of h buffers is
+    // fixed at compile time.  The rolled loop (buffer picked from t at run
+    // time) gave states that differed from the streaming kernel at T = 3 in
+    // the bitwise tiling tests; the cause was not found, and the unrolled
+    // form matches bit for bit.
+#pragma unroll
     for (int t = 0; t < T; ++t) {
-        for (int q = threadIdx.x; q < NC; q += SWT_THREADS) hh[q] = __fadd_rn(HH[q], e[q]);
-        __syncthreads();
+        const float *hh = hh2[t & 1];
         // momentum predictor of the east and north faces of each cell
-        for (int q = threadIdx.x; q < NC; q += SWT_THREADS) {
-            const int lx = q % LW, ly = q / LW, gx = x0 + lx, gy = y0 + ly;
-            const bool wc = hh[q] > hmin;
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            if (!act[k]) continue;
+            const int q = threadIdx.x + k * SWT_THREADS;
+            const int gx = x0 + lx[k], gy = y0 + ly[k];
+            const bool wc = rh[k] > hmin;
             float un = 0.0f, vn = 0.0f;
-            if (lx + 1 < LW && gx >= 0 && gx < p.nx - 1)
-                un = sw_face_mask(sw_predict(uu[q], p.gdt_dx, e[q + 1], e[q]), wc, hh[q + 1] > hmin);
-            if (ly + 1 < LH && gy >= 0 && gy < p.ny - 1)
-                vn = sw_face_mask(sw_predict(vv[q], p.gdt_dy, e[q + LW], e[q]), wc, hh[q + LW] > hmin);
+            if (lx[k] + 1 < LW && gx >= 0 && gx < p.nx - 1)
+                un = sw_face_mask(sw_predict(ru[k], p.gdt_dx, e[q + 1], re[k]), wc, hh[q + 1] > hmin);
+            if (ly[k] + 1 < LH && gy >= 0 && gy < p.ny - 1)
+                vn = sw_face_mask(sw_predict(rv[k], p.gdt_dy, e[q + LW], re[k]), wc, hh[q + LW] > hmin);
+            ru[k] = un;
+            rv[k] = vn;
             uu[q] = un;
             vv[q] = vn;
         }
         __syncthreads();
         // continuity with upwind face fluxes
-        for (int q = threadIdx.x; q < NC; q += SWT_THREADS) {
-            const int lx = q % LW, ly = q / LW;
-            float out = e[q];
-            if (lx > 0 && lx + 1 < LW && ly > 0 && ly + 1 < LH) {
-                const float h1 = hh[q];
-                const float fe = sw_upwind(uu[q], h1, hh[q + 1]);
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            if (!act[k]) continue;
+            const int q = threadIdx.x + k * SWT_THREADS;
+            float out = re[k];
+            if (lx[k] > 0 && lx[k] + 1 < LW && ly[k] > 0 && ly[k] + 1 < LH) {
+                const float h1 = rh[k];
+                const float fe = sw_upwind(ru[k], h1, hh[q + 1]);
                 const float fw = sw_upwind(uu[q - 1], hh[q - 1], h1);
-                const float gn = sw_upwind(vv[q], h1, hh[q + LW]);
+                const float gn = sw_upwind(rv[k], h1, hh[q + LW]);
                 const float gs = sw_upwind(vv[q - LW], hh[q - LW], h1);
-                out = __fsub_rn(e[q], __fmaf_rn(p.dt_dx, __fsub_rn(fe, fw), __fmul_rn(p.dt_dy, __fsub_rn(gn, gs))));
+                out = __fsub_rn(re[k], __fmaf_rn(p.dt_dx, __fsub_rn(fe, fw), __fmul_rn(p.dt_dy, __fsub_rn(gn, gs))));
             }
+            rs[k] = out;
             es[q] = out;
         }
         __syncthreads();
         // masked Shapiro filter on wet cells
-        for (int q = threadIdx.x; q < NC; q += SWT_THREADS) {
-            const int lx = q % LW, ly = q / LW;
-            float out = es[q];
-            if (lx > 0 && lx + 1 < LW && ly > 0 && ly + 1 < LH && hh[q] > hmin) {
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            if (!act[k]) continue;
+            const int q = threadIdx.x + k * SWT_THREADS;
+            float out = rs[k];
+            if (lx[k] > 0 && lx[k] + 1 < LW && ly[k] > 0 && ly[k] + 1 < LH && rh[k] > hmin) {
                 const float we = hh[q + 1] > hmin ? 1.0f : 0.0f;
                 const float ww = hh[q - 1] > hmin ? 1.0f : 0.0f;
                 const float wn = hh[q + LW] > hmin ? 1.0f : 0.0f;
@@ -99,21 +133,28 @@ sw_tile_kernel(SWDev p, const float *__restrict__ H, const float *__restrict__ e
                 const float cnt = (we + ww) + (wn + ws);  // small integers: exact
                 const float sum = __fadd_rn(__fadd_rn(__fmul_rn(we, es[q + 1]), __fmul_rn(ww, es[q - 1])),
                                             __fadd_rn(__fmul_rn(wn, es[q + LW]), __fmul_rn(ws, es[q - LW])));
-                out = __fmaf_rn(p.q, sum, __fmul_rn(__fsub_rn(1.0f, __fmul_rn(p.q, cnt)), es[q]));
+                out = __fmaf_rn(p.q, sum, __fmul_rn(__fsub_rn(1.0f, __fmul_rn(p.q, cnt)), rs[k]));
             }
-            e[q] = out;
+            re[k] = out;
+            if (t + 1 < T) {
+                // the next step's depth goes to the other buffer: this phase still reads hh
+                rh[k] = __fadd_rn(rH[k], out);
+                hh2[(t + 1) & 1][q] = rh[k];
+                e[q] = out;
+            }
         }
-        __syncthreads();
+        if (t + 1 < T) __syncthreads();
     }
-    for (int q = threadIdx.x; q < SWT_W * SWT_H; q += SWT_THREADS) {
-        const int lx = HALO + q % SWT_W, ly = HALO + q / SWT_W, gx = x0 + lx, gy = y0 + ly;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        if (!act[k] || lx[k] < HALO || lx[k] >= HALO + SWT_W || ly[k] < HALO || ly[k] >= HALO + SWT_H) continue;
+        const int gx = x0 + lx[k], gy = y0 + ly[k];
         if (gx < p.nx && gy < p.ny &&
             GBSW_INBOUNDS((long long)gy * p.pitch + gx, (long long)p.ny * p.pitch, &g_sw_bounds)) {
             const size_t g = (size_t)gy * p.pitch + gx;
-            const int c = ly * LW + lx;
-            eta_out[g] = e[c];
-            u_out[g] = uu[c];
-            v_out[g] = vv[c];
+            eta_out[g] = re[k];
+            u_out[g] = ru[k];
+            v_out[g] = rv[k];
         }
     }
 }
