@@ -581,8 +581,9 @@ def les_object(args, local):
     out = {
         "workload": f"UFLES 256x256x128, dx 4 m, dt 0.025 s, 20 % building cover (building seed {args.les_seed}), "
                     f"SOR omega 1.8 to a 1e-6 relative FP64 residual checked every {args.check_every} iterations; "
-                    f"{args.les_spinup} spin-up steps, then {n} states compared, evenly spaced over steps "
-                    f"{args.les_spinup + 1}..{args.les_spinup + args.les_horizon}",
+                    f"{args.les_spinup} spin-up steps, then {n} of the steps "
+                    f"{args.les_spinup + 1}..{args.les_spinup + args.les_horizon} compared"
+                    + (" (every step)" if n == args.les_horizon else " (one per equal block)"),
         "metric": "LES step time at 1e-6 residual, learned vs previous-pressure warm start",
         "unit": "ms/step", "higher_is_better": False, "dtype": "f32 sweeps, f64 pressure and norms",
         "plain": {"ms_per_step": mean("plain_ms"), "sor_iters_per_step": it_plain,
@@ -601,7 +602,8 @@ def les_object(args, local):
                      "per_unit": f"12 B/cell/iteration x {cells} cells (solve time / iterations, checks included)",
                      "traffic": traffic, "traffic_note": note or "DRAM bytes per iteration, warm L2",
                      "hbm_frac": ach / _peaks()[0]},
-        "rows": rows,
+        "per_step": {k: [r[k] for r in rows] for k in ("step", "plain_iters", "nn_iters")}
+                    | {k: [round(r[k], 2) for r in rows] for k in ("plain_ms", "nn_ms")},
     }
     out["learned"]["speedup"] = out["plain"]["ms_per_step"] / out["learned"]["ms_per_step"]
     if not args.no_cpu_baseline:
@@ -644,7 +646,7 @@ def run_les(args, rank, world, local, learned):
                                                           "between sweeps; that reuse is the method's own"},
             "clocks": obj["clocks"], "sor_iters_per_step": obj[key]["sor_iters_per_step"],
             "roofline": obj["roofline"], "cpu_baseline": obj.get("cpu_baseline"), "e2e": obj["e2e"][key],
-            "plain": obj["plain"], "learned": obj["learned"], "rows": obj["rows"]}
+            "plain": obj["plain"], "learned": obj["learned"], "per_step": obj["per_step"]}
     print(json.dumps(line), flush=True)
 
 
@@ -878,7 +880,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-les", action="store_true", help="default workload: leave out the UFLES object")
     ap.add_argument("--les-spinup", type=int, default=20, help="UFLES object: spin-up steps before the comparison")
-    ap.add_argument("--les-steps", type=int, default=10, help="UFLES object: compared states")
+    ap.add_argument("--les-steps", type=int, default=180,
+                    help="UFLES object: compared states (180: every step of the horizon)")
     ap.add_argument("--les-horizon", type=int, default=180,
                     help="UFLES object: steps after the spin-up over which the compared states are spread")
     ap.add_argument("--les-e2e-steps", type=int, default=3, help="UFLES object: steps per end-to-end timing")
