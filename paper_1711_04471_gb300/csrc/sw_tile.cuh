@@ -17,7 +17,7 @@
 // two kernels give bitwise the same state.
 //
 // Compared with the streaming kernel, a launch has no row-by-row pipeline:
-// its latency is one load, 4T short phases and one store, which is what
+// its latency is one load, 3T short phases and one store, which is what
 // the small grids of the paper (500^2 .. 2000^2, a few MB) need.
 #pragma once
 
@@ -83,10 +83,14 @@ sw_tile_kernel(SWDev p, const float *__restrict__ H, const float *__restrict__ e
 #pragma unroll
     for (int t = 0; t < T; ++t) {
         const float *hh = hh2[t & 1];
+        // Rows that can still reach the written block: those within 2 (T - t)
+        // of it for the predictor, one fewer per later phase.  The other
+        // rows hold discarded halo, so they are skipped.
+        const int B_LO = 2 * t, C_LO = 2 * t + 1, D_LO = 2 * t + 2;  // constants once the loop is unrolled
         // momentum predictor of the east and north faces of each cell
 #pragma unroll
         for (int k = 0; k < PER; ++k) {
-            if (!act[k]) continue;
+            if (!act[k] || ly[k] < B_LO || ly[k] >= LH - B_LO) continue;
             const int q = threadIdx.x + k * SWT_THREADS;
             const int gx = x0 + lx[k], gy = y0 + ly[k];
             const bool wc = rh[k] > hmin;
@@ -104,7 +108,7 @@ sw_tile_kernel(SWDev p, const float *__restrict__ H, const float *__restrict__ e
         // continuity with upwind face fluxes
 #pragma unroll
         for (int k = 0; k < PER; ++k) {
-            if (!act[k]) continue;
+            if (!act[k] || ly[k] < C_LO || ly[k] >= LH - C_LO) continue;
             const int q = threadIdx.x + k * SWT_THREADS;
             float out = re[k];
             if (lx[k] > 0 && lx[k] + 1 < LW && ly[k] > 0 && ly[k] + 1 < LH) {
@@ -122,7 +126,7 @@ sw_tile_kernel(SWDev p, const float *__restrict__ H, const float *__restrict__ e
         // masked Shapiro filter on wet cells
 #pragma unroll
         for (int k = 0; k < PER; ++k) {
-            if (!act[k]) continue;
+            if (!act[k] || ly[k] < D_LO || ly[k] >= LH - D_LO) continue;
             const int q = threadIdx.x + k * SWT_THREADS;
             float out = rs[k];
             if (lx[k] > 0 && lx[k] + 1 < LW && ly[k] > 0 && ly[k] + 1 < LH && rh[k] > hmin) {
