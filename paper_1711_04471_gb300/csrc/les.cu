@@ -2,15 +2,17 @@
 // velfg -> feedbf -> les -> adam -> press, on the GPU.
 //
 // Kernels per step:
-//   les_velnw_kernel      u = u* - dt grad p                     (velnw)
-//   les_bc_{x,y,z}_kernel inflow face and ghost layer            (bondv1)
-//   les_nut_kernel        Smagorinsky nu_t incl. ghost layer     (les, part 1)
-//   les_predict_kernel    advection + Goldstein forcing + viscous
-//                         stress divergence + Adams-Bashforth    (velfg, feedbf, les, adam)
-//   les_rhs_kernel        b = div(u*) / dt                       (press, right-hand side)
-//   PoissonSolver         red-black SOR to the FP64 tolerance    (press)
+//   les_velnw_kernel         u = u* - dt grad p                  (velnw)
+//   les_predict_tile_kernel  ghost layer + Smagorinsky nu_t +
+//                            advection + Goldstein forcing + viscous
+//                            stress divergence + Adams-Bashforth (bondv1, les, velfg, feedbf, adam)
+//   les_rhs_kernel           b = div(u*) / dt                    (press, right-hand side)
+//   PoissonSolver            red-black SOR to the FP64 tolerance (press)
 // The paper's compiler emitted 29 map and 4 reduction kernels for this
-// loop; here velfg, feedbf, the viscous terms and adam are one kernel.
+// loop; here everything between velnw and the right-hand side is one
+// kernel.  velnw stays apart: its pressure differences are FP64, which
+// runs at a small fraction of the FP32 rate on this GPU, and a fused tile
+// would recompute them on every halo cell.
 //
 // Layout: every field is a (nz+2) x (ny+2) x pitch FP32 array with one
 // ghost layer (pitch = nx+2 rounded up to 32), cell (i,j,k) at
@@ -64,205 +66,308 @@ __global__ void les_velnw_kernel(LDev q, const double *__restrict__ p, float *__
     if (k < d.nz) w[c] -= q.c_grad * (float)(p[c + d.plane] - pc);
 }
 
-// bondv1, x planes: inflow profile, v = w = 0 at the inflow, zero gradient
-// at the outflow.  grid (ceil(ny/128), nz), block 128.
-__global__ void les_bc_x_kernel(LDev q, const float *__restrict__ uin, float *u, float *v, float *w)
-{
-    const PDims &d = q.d;
-    const int j = blockIdx.x * blockDim.x + threadIdx.x + 1;
-    const int k = blockIdx.y + 1;
-    if (j > d.ny) return;
-    const long long c0 = L(d, 0, j, k), cn = L(d, d.nx, j, k);
-    u[c0] = uin[k];
-    u[cn + 1] = u[cn];
-    v[c0] = -v[c0 + 1];
-    v[cn + 1] = v[cn];
-    w[c0] = -w[c0 + 1];
-    w[cn + 1] = w[cn];
-}
+// ---------------------------------------------------------------- fused predictor
+// bondv1 + les (nu_t) + velfg + feedbf + viscous terms + adam in one pass.
+// A CTA owns LT_X x LT_Y columns of cells and marches up a chunk of LT_KZ
+// planes.  Shared memory holds a ring of LT_US planes of u, v, w (after
+// velnw) with a 2-cell halo in x and y, and a ring of LT_ES planes of nu_t
+// with a 1-cell halo; each plane step loads plane k+2, forms nu_t on plane
+// k+1 and predicts plane k, with two barriers.  The ghost layer of bondv1
+// is formed while loading (never stored): inflow profile and reflected v, w
+// at i = 0, zero gradient at i = nx+1, periodic rows, no slip at the ground,
+// free slip at the lid, w = 0 on the ground and lid faces; a ghost nu_t is
+// that of its zero-gradient / periodic source.  The arithmetic of every
+// term is that of the oracle's subroutines (Sec. 6.3.1).
+constexpr int LT_X = 32, LT_Y = 8, LT_THREADS = LT_X * LT_Y;
+constexpr int LT_HX = LT_X + 4, LT_HY = LT_Y + 4, LT_HN = LT_HX * LT_HY;  // velocity planes, halo 2
+constexpr int LT_EX = LT_X + 2, LT_EY = LT_Y + 2, LT_EN = LT_EX * LT_EY;  // nu_t planes, halo 1
+constexpr int LT_US = 5, LT_ES = 3;  // ring slots: planes k-2 .. k+2 and k-1 .. k+1 of plane step k
+constexpr int LT_KZ = 8;             // planes per CTA (8 and 16 tie on large grids; 8 keeps small grids parallel)
 
-// bondv1, y planes: periodic.  grid (ceil((nx+2)/128), nz), block 128.
-__global__ void les_bc_y_kernel(LDev q, float *u, float *v, float *w)
-{
-    const PDims &d = q.d;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int k = blockIdx.y + 1;
-    if (i > d.nx + 1) return;
-    const long long s0 = L(d, i, 0, k), s1 = L(d, i, 1, k), sn = L(d, i, d.ny, k), sn1 = L(d, i, d.ny + 1, k);
-    u[s0] = u[sn];
-    u[sn1] = u[s1];
-    v[s0] = v[sn];
-    v[sn1] = v[s1];
-    w[s0] = w[sn];
-    w[sn1] = w[s1];
-}
+struct LesTileSmem {
+    float vel[LT_US][3][LT_HN];  // u, v, w
+    float nut[LT_ES][LT_EN];
+};
 
-// bondv1, z planes: no slip at the ground, free slip at the lid.
-// grid (ceil((nx+2)/128), ny+2), block 128.
-__global__ void les_bc_z_kernel(LDev q, float *u, float *v, float *w)
-{
-    const PDims &d = q.d;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y;
-    if (i > d.nx + 1) return;
-    const long long g0 = L(d, i, j, 0), g1 = g0 + d.plane;
-    const long long t0 = L(d, i, j, d.nz), t1 = t0 + d.plane;
-    u[g0] = -u[g1];
-    v[g0] = -v[g1];
-    w[g0] = 0.0f;
-    u[t1] = u[t0];
-    v[t1] = v[t0];
-    w[t0] = 0.0f;
-    w[t1] = 0.0f;
-}
+__device__ __forceinline__ int lt_uslot(int k) { return (k + LT_US) % LT_US; }
+__device__ __forceinline__ int lt_eslot(int k) { return (k + LT_ES) % LT_ES; }
 
-__device__ __forceinline__ float s12e(const PDims &d, float rdx, const float *u, const float *v, int i, int j, int k)
-{
-    return 0.5f * ((u[L(d, i, j + 1, k)] - u[L(d, i, j, k)]) + (v[L(d, i + 1, j, k)] - v[L(d, i, j, k)])) * rdx;
-}
-__device__ __forceinline__ float s13e(const PDims &d, float rdx, const float *u, const float *w, int i, int j, int k)
-{
-    return 0.5f * ((u[L(d, i, j, k + 1)] - u[L(d, i, j, k)]) + (w[L(d, i + 1, j, k)] - w[L(d, i, j, k)])) * rdx;
-}
-__device__ __forceinline__ float s23e(const PDims &d, float rdx, const float *v, const float *w, int i, int j, int k)
-{
-    return 0.5f * ((v[L(d, i, j, k + 1)] - v[L(d, i, j, k)]) + (w[L(d, i, j + 1, k)] - w[L(d, i, j, k)])) * rdx;
-}
+constexpr int LT_LPT = (LT_HN + LT_THREADS - 1) / LT_THREADS;  // velocity cells a thread loads per plane
+constexpr int LT_NPT = (LT_EN + LT_THREADS - 1) / LT_THREADS;  // nu_t cells a thread forms per plane
 
-// les, part 1: nu_t = (cs dx)^2 sqrt(2 S:S) on the interior and the ghost
-// layer (a ghost takes the value of its zero-gradient / periodic source).
-// grid (ceil((nx+2)/64), ny+2, nz+2), block 64.
-__global__ void les_nut_kernel(LDev q, const float *__restrict__ u, const float *__restrict__ v,
-                               const float *__restrict__ w, float *__restrict__ nut)
+// The cells a thread loads of every velocity plane and forms of every nu_t
+// plane, fixed for the whole march (so no plane step repeats the index
+// arithmetic).
+struct LtMap {
+    int src[LT_LPT];   // in-plane offset of the loaded cell's source (row wrapped, column clamped); -1: zero
+    unsigned inflow;   // bit c: loaded cell c is on the inflow face i = 0
+    int o[LT_NPT];     // velocity-plane offset of nu_t cell c's source (column clamped); -1: not formed
+    int out[LT_NPT];   // in-plane offset of nu_t cell c in the output field; -1: not this CTA's cell
+};
+
+__device__ __forceinline__ LtMap lt_map(const PDims &d, int i0, int j0)
 {
-    const PDims &d = q.d;
-    const int gi = blockIdx.x * blockDim.x + threadIdx.x;
-    const int gj = blockIdx.y, gk = blockIdx.z;
-    if (gi > d.nx + 1) return;
-    const int i = min(max(gi, 1), d.nx);
-    const int j = gj == 0 ? d.ny : (gj == d.ny + 1 ? 1 : gj);
-    const int k = min(max(gk, 1), d.nz);
-    const float r = q.rdx;
-    const float s11 = (u[L(d, i, j, k)] - u[L(d, i - 1, j, k)]) * r;
-    const float s22 = (v[L(d, i, j, k)] - v[L(d, i, j - 1, k)]) * r;
-    const float s33 = (w[L(d, i, j, k)] - w[L(d, i, j, k - 1)]) * r;
-    float a12 = 0.0f, a13 = 0.0f, a23 = 0.0f;
+    LtMap m;
+    m.inflow = 0;
 #pragma unroll
-    for (int a = -1; a <= 0; ++a)
-#pragma unroll
-        for (int b = -1; b <= 0; ++b) {
-            const float e12 = s12e(d, r, u, v, i + a, j + b, k);
-            const float e13 = s13e(d, r, u, w, i + a, j, k + b);
-            const float e23 = s23e(d, r, v, w, i, j + a, k + b);
-            a12 += e12 * e12;
-            a13 += e13 * e13;
-            a23 += e23 * e23;
+    for (int c = 0; c < LT_LPT; ++c) {
+        const int idx = threadIdx.x + c * LT_THREADS;
+        const int lx = idx % LT_HX, ly = idx / LT_HX;
+        const int i = i0 - 1 + lx, j = j0 - 1 + ly;
+        m.src[c] = -1;
+        if (idx < LT_HN && i >= 0 && i <= d.nx + 1) {  // columns outside the ghost layer are never read
+            int jw = (j - 1) % d.ny;
+            if (jw < 0) jw += d.ny;
+            jw += 1;  // periodic rows
+            const int ic = i == 0 ? 1 : (i == d.nx + 1 ? d.nx : i);
+            m.src[c] = jw * d.pitch + ic;
+            if (i == 0) m.inflow |= 1u << c;
         }
-    const float ss = 2.0f * (s11 * s11 + s22 * s22 + s33 * s33) + (a12 + a13 + a23);
-    nut[L(d, gi, gj, gk)] = q.l2 * sqrtf(ss);
+    }
+#pragma unroll
+    for (int c = 0; c < LT_NPT; ++c) {
+        const int idx = threadIdx.x + c * LT_THREADS;
+        const int ex = idx % LT_EX, ey = idx / LT_EX;
+        const int i = i0 + ex, j = j0 + ey;
+        m.o[c] = -1;
+        m.out[c] = -1;
+        if (idx < LT_EN && i <= d.nx + 1) {  // past the ghost column: never read
+            const int ic = min(max(i, 1), d.nx);
+            m.o[c] = (ey + 1) * LT_HX + (ic - i0 + 1);
+            if (ex >= 1 && ex <= LT_X && ey >= 1 && ey <= LT_Y && i <= d.nx && j <= d.ny) m.out[c] = j * d.pitch + i;
+        }
+    }
+    return m;
 }
 
-// velfg + feedbf + viscous terms + adam on the three faces owned by cell
-// (i,j,k): reads u^n (with ghosts) and nu_t, writes u* to the other buffer
-// set and updates F_old and the Goldstein integrals in place.
-// grid (ceil(nx/32), ceil(ny/4), nz), block (32, 4).
-__global__ void __launch_bounds__(128)
-les_predict_kernel(LDev q, int first, const float *__restrict__ u, const float *__restrict__ v,
-                   const float *__restrict__ w, const float *__restrict__ nut, const uint8_t *__restrict__ face,
-                   float *__restrict__ us, float *__restrict__ vs, float *__restrict__ ws, float *__restrict__ fuo,
-                   float *__restrict__ fvo, float *__restrict__ fwo, float *__restrict__ gu, float *__restrict__ gv,
-                   float *__restrict__ gw)
+// Velocity plane kk (0 .. nz+1) of the tile after bondv1, into its slot:
+// ground ghost reflected u, v; lid ghost copied u, v; w = 0 on both and on
+// the lid face; inflow profile and reflected v, w at i = 0.
+__device__ __forceinline__ void lt_load_plane(const LDev &q, LesTileSmem &sm, const LtMap &m, int kk,
+                                              const float *__restrict__ u, const float *__restrict__ v,
+                                              const float *__restrict__ w, const float *__restrict__ uin)
 {
     const PDims &d = q.d;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
-    const int k = blockIdx.z + 1;
-    if (i > d.nx || j > d.ny) return;
+    if (kk < 0 || kk > d.nz + 1) return;
+    float *pu = sm.vel[lt_uslot(kk)][0], *pv = sm.vel[lt_uslot(kk)][1], *pw = sm.vel[lt_uslot(kk)][2];
+    const int kc = kk == 0 ? 1 : (kk == d.nz + 1 ? d.nz : kk);
+    const bool ground = kk == 0, wzero = kk == 0 || kk >= d.nz;
+    const long long base = (long long)kc * d.plane;
+    const float uin_k = uin[kc];
+#pragma unroll
+    for (int c = 0; c < LT_LPT; ++c) {
+        const int idx = threadIdx.x + c * LT_THREADS;
+        if (idx >= LT_HN) continue;
+        float a = 0.0f, b = 0.0f, cw = 0.0f;
+        if (m.src[c] >= 0) {
+            const long long cc = base + m.src[c];
+            const bool in = (m.inflow >> c) & 1u;
+            const float uu = in ? uin_k : u[cc];
+            float vv = v[cc], ww = w[cc];
+            if (in) {
+                vv = -vv;
+                ww = -ww;
+            }
+            a = ground ? -uu : uu;
+            b = ground ? -vv : vv;
+            cw = wzero ? 0.0f : ww;
+        }
+        pu[idx] = a;
+        pv[idx] = b;
+        pw[idx] = cw;
+    }
+}
+
+// nu_t = (cs dx)^2 sqrt(2 S:S) on plane kk (0 .. nz+1) of the tile and its
+// 1-cell halo, from velocity planes kc-1 .. kc+1 (kc = kk clamped to
+// 1 .. nz; a ghost column takes the value of i clamped to 1 .. nx; rows
+// are periodic through the loaded planes).  The CTA's own interior cells
+// are also written to nut_out when write is set.
+__device__ __forceinline__ void lt_nut_plane(const LDev &q, LesTileSmem &sm, const LtMap &m, int kk, bool write,
+                                             float *__restrict__ nut_out)
+{
+    const PDims &d = q.d;
+    if (kk < 0 || kk > d.nz + 1) return;
+    const int kc = min(max(kk, 1), d.nz);
+    const float *um = sm.vel[lt_uslot(kc - 1)][0], *uc = sm.vel[lt_uslot(kc)][0], *up = sm.vel[lt_uslot(kc + 1)][0];
+    const float *vm = sm.vel[lt_uslot(kc - 1)][1], *vc = sm.vel[lt_uslot(kc)][1], *vp = sm.vel[lt_uslot(kc + 1)][1];
+    const float *wm = sm.vel[lt_uslot(kc - 1)][2], *wc = sm.vel[lt_uslot(kc)][2];
+    float *ne = sm.nut[lt_eslot(kk)];
+    const float r = q.rdx;
+    const long long base = (long long)kk * d.plane;
+#pragma unroll
+    for (int c = 0; c < LT_NPT; ++c) {
+        const int o = m.o[c];
+        if (o < 0) continue;
+        // velocity of cell (ic+a, j+b) on plane kc, kc-1 (m) or kc+1 (p)
+        auto U = [&](int a, int b) { return uc[o + b * LT_HX + a]; };
+        auto V = [&](int a, int b) { return vc[o + b * LT_HX + a]; };
+        auto W = [&](int a, int b) { return wc[o + b * LT_HX + a]; };
+        const float s11 = (U(0, 0) - U(-1, 0)) * r;
+        const float s22 = (V(0, 0) - V(0, -1)) * r;
+        const float s33 = (W(0, 0) - wm[o]) * r;
+        float a12 = 0.0f, a13 = 0.0f, a23 = 0.0f;
+#pragma unroll
+        for (int a = -1; a <= 0; ++a)
+#pragma unroll
+            for (int b = -1; b <= 0; ++b) {
+                // edges: xy at (ic+a, j+b, kc), xz at (ic+a, j, kc+b), yz at (ic, j+a, kc+b)
+                const float *uz0 = b < 0 ? um : uc, *uz1 = b < 0 ? uc : up;
+                const float *wz0 = b < 0 ? wm : wc;
+                const float *vz0 = b < 0 ? vm : vc, *vz1 = b < 0 ? vc : vp;
+                const float e12 = 0.5f * ((U(a, b + 1) - U(a, b)) + (V(a + 1, b) - V(a, b))) * r;
+                const float e13 = 0.5f * ((uz1[o + a] - uz0[o + a]) + (wz0[o + a + 1] - wz0[o + a])) * r;
+                const float e23 = 0.5f * ((vz1[o + a * LT_HX] - vz0[o + a * LT_HX]) +
+                                          (wz0[o + (a + 1) * LT_HX] - wz0[o + a * LT_HX])) * r;
+                a12 += e12 * e12;
+                a13 += e13 * e13;
+                a23 += e23 * e23;
+            }
+        const float ss = 2.0f * (s11 * s11 + s22 * s22 + s33 * s33) + (a12 + a13 + a23);
+        const float nt = q.l2 * sqrtf(ss);
+        ne[threadIdx.x + c * LT_THREADS] = nt;
+        if (write && m.out[c] >= 0) nut_out[base + m.out[c]] = nt;
+    }
+}
+
+// velfg + feedbf + viscous terms + adam on the three faces owned by the
+// thread's cell (i, j, k) of plane k, from the velocity and nu_t rings.
+__device__ __forceinline__ void lt_predict_cell(const LDev &q, const LesTileSmem &sm, int k, int i, int j, int o,
+                                                int on, bool first, const uint8_t *__restrict__ face,
+                                                float *__restrict__ us, float *__restrict__ vs,
+                                                float *__restrict__ ws, float *__restrict__ fuo,
+                                                float *__restrict__ fvo, float *__restrict__ fwo,
+                                                float *__restrict__ gu, float *__restrict__ gv, float *__restrict__ gw)
+{
+    const PDims &d = q.d;
     const float r = q.rdx, nu = q.nu;
+    const float *vel[3] = {sm.vel[lt_uslot(k - 1)][0], sm.vel[lt_uslot(k)][0], sm.vel[lt_uslot(k + 1)][0]};
+    const float *nut[3] = {sm.nut[lt_eslot(k - 1)], sm.nut[lt_eslot(k)], sm.nut[lt_eslot(k + 1)]};
+    // value at cell (i+x, j+y, k+z), |x|, |y|, |z| <= 1 (field 0 u, 1 v, 2 w)
+    auto F = [&](int f, int x, int y, int z) { return vel[z + 1][f * LT_HN + o + y * LT_HX + x]; };
+    auto U = [&](int x, int y, int z) { return F(0, x, y, z); };
+    auto V = [&](int x, int y, int z) { return F(1, x, y, z); };
+    auto W = [&](int x, int y, int z) { return F(2, x, y, z); };
+    auto NE = [&](int x, int y, int z) { return nu + nut[z + 1][on + y * LT_EX + x]; };
+    // stresses at their natural points, offsets relative to the cell
+    auto T11 = [&](int x, int y, int z) { return 2.0f * NE(x, y, z) * (U(x, y, z) - U(x - 1, y, z)) * r; };
+    auto T22 = [&](int x, int y, int z) { return 2.0f * NE(x, y, z) * (V(x, y, z) - V(x, y - 1, z)) * r; };
+    auto T33 = [&](int x, int y, int z) { return 2.0f * NE(x, y, z) * (W(x, y, z) - W(x, y, z - 1)) * r; };
+    auto T12 = [&](int x, int y, int z) {  // xy edge east-north of cell (x, y, z)
+        const float s = 0.5f * ((U(x, y + 1, z) - U(x, y, z)) + (V(x + 1, y, z) - V(x, y, z))) * r;
+        const float ne = 0.25f * ((NE(x, y, z) + NE(x + 1, y, z)) + (NE(x, y + 1, z) + NE(x + 1, y + 1, z)));
+        return 2.0f * ne * s;
+    };
+    auto T13 = [&](int x, int y, int z) {  // xz edge east-top
+        const float s = 0.5f * ((U(x, y, z + 1) - U(x, y, z)) + (W(x + 1, y, z) - W(x, y, z))) * r;
+        const float ne = 0.25f * ((NE(x, y, z) + NE(x + 1, y, z)) + (NE(x, y, z + 1) + NE(x + 1, y, z + 1)));
+        return 2.0f * ne * s;
+    };
+    auto T23 = [&](int x, int y, int z) {  // yz edge north-top
+        const float s = 0.5f * ((V(x, y, z + 1) - V(x, y, z)) + (W(x, y + 1, z) - W(x, y, z))) * r;
+        const float ne = 0.25f * ((NE(x, y, z) + NE(x, y + 1, z)) + (NE(x, y, z + 1) + NE(x, y + 1, z + 1)));
+        return 2.0f * ne * s;
+    };
     const long long c = L(d, i, j, k);
-    const long long sx = 1, sy = d.pitch, sz = d.plane;
-    auto U = [&](long long o) { return u[c + o]; };
-    auto V = [&](long long o) { return v[c + o]; };
-    auto W = [&](long long o) { return w[c + o]; };
-    auto NE = [&](long long o) { return nu + nut[c + o]; };
-    // stresses at their natural points, offsets relative to cell c
-    auto T11 = [&](long long o) { return 2.0f * NE(o) * (U(o) - U(o - sx)) * r; };
-    auto T22 = [&](long long o) { return 2.0f * NE(o) * (V(o) - V(o - sy)) * r; };
-    auto T33 = [&](long long o) { return 2.0f * NE(o) * (W(o) - W(o - sz)) * r; };
-    auto T12 = [&](long long o) {  // xy edge east-north of cell c+o
-        const float s = 0.5f * ((U(o + sy) - U(o)) + (V(o + sx) - V(o))) * r;
-        const float ne = 0.25f * ((NE(o) + NE(o + sx)) + (NE(o + sy) + NE(o + sx + sy)));
-        return 2.0f * ne * s;
-    };
-    auto T13 = [&](long long o) {  // xz edge east-top of cell c+o
-        const float s = 0.5f * ((U(o + sz) - U(o)) + (W(o + sx) - W(o))) * r;
-        const float ne = 0.25f * ((NE(o) + NE(o + sx)) + (NE(o + sz) + NE(o + sx + sz)));
-        return 2.0f * ne * s;
-    };
-    auto T23 = [&](long long o) {  // yz edge north-top of cell c+o
-        const float s = 0.5f * ((V(o + sz) - V(o)) + (W(o + sy) - W(o))) * r;
-        const float ne = 0.25f * ((NE(o) + NE(o + sy)) + (NE(o + sz) + NE(o + sy + sz)));
-        return 2.0f * ne * s;
-    };
     const uint8_t fl = face[c];
     const float dt = q.dt;
-    const float t12 = T12(0), t13 = T13(0), t23 = T23(0);
-
+    const float t12 = T12(0, 0, 0), t13 = T13(0, 0, 0), t23 = T23(0, 0, 0);
     // ---- u face (i+1/2, j, k)
     {
-        const float ue = 0.5f * (U(0) + U(sx)), uw = 0.5f * (U(-sx) + U(0));
-        const float un = 0.5f * (U(0) + U(sy)) * 0.5f * (V(0) + V(sx));
-        const float us_ = 0.5f * (U(-sy) + U(0)) * 0.5f * (V(-sy) + V(sx - sy));
-        const float ut = 0.5f * (U(0) + U(sz)) * 0.5f * (W(0) + W(sx));
-        const float ub = 0.5f * (U(-sz) + U(0)) * 0.5f * (W(-sz) + W(sx - sz));
+        const float ue = 0.5f * (U(0, 0, 0) + U(1, 0, 0)), uw = 0.5f * (U(-1, 0, 0) + U(0, 0, 0));
+        const float un = 0.5f * (U(0, 0, 0) + U(0, 1, 0)) * 0.5f * (V(0, 0, 0) + V(1, 0, 0));
+        const float us_ = 0.5f * (U(0, -1, 0) + U(0, 0, 0)) * 0.5f * (V(0, -1, 0) + V(1, -1, 0));
+        const float ut = 0.5f * (U(0, 0, 0) + U(0, 0, 1)) * 0.5f * (W(0, 0, 0) + W(1, 0, 0));
+        const float ub = 0.5f * (U(0, 0, -1) + U(0, 0, 0)) * 0.5f * (W(0, 0, -1) + W(1, 0, -1));
         float f = -r * ((ue * ue - uw * uw) + (un - us_) + (ut - ub));
         if (fl & FACE_U) {
-            const float g = gu[c] + dt * U(0);
+            const float g = gu[c] + dt * U(0, 0, 0);
             gu[c] = g;
-            f += q.alpha * g + q.beta * U(0);
+            f += q.alpha * g + q.beta * U(0, 0, 0);
         }
-        f += r * ((T11(sx) - T11(0)) + (t12 - T12(-sy)) + (t13 - T13(-sz)));
+        f += r * ((T11(1, 0, 0) - T11(0, 0, 0)) + (t12 - T12(0, -1, 0)) + (t13 - T13(0, 0, -1)));
         const float fo = fuo[c];
-        us[c] = U(0) + dt * (first ? f : 1.5f * f - 0.5f * fo);
+        us[c] = U(0, 0, 0) + dt * (first ? f : 1.5f * f - 0.5f * fo);
         fuo[c] = f;
     }
     // ---- v face (i, j+1/2, k)
     {
-        const float ve = 0.5f * (V(0) + V(sx)) * 0.5f * (U(0) + U(sy));
-        const float vw = 0.5f * (V(-sx) + V(0)) * 0.5f * (U(-sx) + U(sy - sx));
-        const float vn = 0.5f * (V(0) + V(sy)), vs_ = 0.5f * (V(-sy) + V(0));
-        const float vt = 0.5f * (V(0) + V(sz)) * 0.5f * (W(0) + W(sy));
-        const float vb = 0.5f * (V(-sz) + V(0)) * 0.5f * (W(-sz) + W(sy - sz));
+        const float ve = 0.5f * (V(0, 0, 0) + V(1, 0, 0)) * 0.5f * (U(0, 0, 0) + U(0, 1, 0));
+        const float vw = 0.5f * (V(-1, 0, 0) + V(0, 0, 0)) * 0.5f * (U(-1, 0, 0) + U(-1, 1, 0));
+        const float vn = 0.5f * (V(0, 0, 0) + V(0, 1, 0)), vs_ = 0.5f * (V(0, -1, 0) + V(0, 0, 0));
+        const float vt = 0.5f * (V(0, 0, 0) + V(0, 0, 1)) * 0.5f * (W(0, 0, 0) + W(0, 1, 0));
+        const float vb = 0.5f * (V(0, 0, -1) + V(0, 0, 0)) * 0.5f * (W(0, 0, -1) + W(0, 1, -1));
         float f = -r * ((ve - vw) + (vn * vn - vs_ * vs_) + (vt - vb));
         if (fl & FACE_V) {
-            const float g = gv[c] + dt * V(0);
+            const float g = gv[c] + dt * V(0, 0, 0);
             gv[c] = g;
-            f += q.alpha * g + q.beta * V(0);
+            f += q.alpha * g + q.beta * V(0, 0, 0);
         }
-        f += r * ((t12 - T12(-sx)) + (T22(sy) - T22(0)) + (t23 - T23(-sz)));
+        f += r * ((t12 - T12(-1, 0, 0)) + (T22(0, 1, 0) - T22(0, 0, 0)) + (t23 - T23(0, 0, -1)));
         const float fo = fvo[c];
-        vs[c] = V(0) + dt * (first ? f : 1.5f * f - 0.5f * fo);
+        vs[c] = V(0, 0, 0) + dt * (first ? f : 1.5f * f - 0.5f * fo);
         fvo[c] = f;
     }
     // ---- w face (i, j, k+1/2)
     if (k < d.nz) {
-        const float we = 0.5f * (W(0) + W(sx)) * 0.5f * (U(0) + U(sz));
-        const float ww = 0.5f * (W(-sx) + W(0)) * 0.5f * (U(-sx) + U(sz - sx));
-        const float wn = 0.5f * (W(0) + W(sy)) * 0.5f * (V(0) + V(sz));
-        const float ws_ = 0.5f * (W(-sy) + W(0)) * 0.5f * (V(-sy) + V(sz - sy));
-        const float wt = 0.5f * (W(0) + W(sz)), wb = 0.5f * (W(-sz) + W(0));
+        const float we = 0.5f * (W(0, 0, 0) + W(1, 0, 0)) * 0.5f * (U(0, 0, 0) + U(0, 0, 1));
+        const float ww = 0.5f * (W(-1, 0, 0) + W(0, 0, 0)) * 0.5f * (U(-1, 0, 0) + U(-1, 0, 1));
+        const float wn = 0.5f * (W(0, 0, 0) + W(0, 1, 0)) * 0.5f * (V(0, 0, 0) + V(0, 0, 1));
+        const float ws_ = 0.5f * (W(0, -1, 0) + W(0, 0, 0)) * 0.5f * (V(0, -1, 0) + V(0, -1, 1));
+        const float wt = 0.5f * (W(0, 0, 0) + W(0, 0, 1)), wb = 0.5f * (W(0, 0, -1) + W(0, 0, 0));
         float f = -r * ((we - ww) + (wn - ws_) + (wt * wt - wb * wb));
         if (fl & FACE_W) {
-            const float g = gw[c] + dt * W(0);
+            const float g = gw[c] + dt * W(0, 0, 0);
             gw[c] = g;
-            f += q.alpha * g + q.beta * W(0);
+            f += q.alpha * g + q.beta * W(0, 0, 0);
         }
-        f += r * ((t13 - T13(-sx)) + (t23 - T23(-sy)) + (T33(sz) - T33(0)));
+        f += r * ((t13 - T13(-1, 0, 0)) + (t23 - T23(0, -1, 0)) + (T33(0, 0, 1) - T33(0, 0, 0)));
         const float fo = fwo[c];
-        ws[c] = W(0) + dt * (first ? f : 1.5f * f - 0.5f * fo);
+        ws[c] = W(0, 0, 0) + dt * (first ? f : 1.5f * f - 0.5f * fo);
         fwo[c] = f;
     }
-    if (i == 1) us[c - 1] = U(-sx);  // the inflow face travels with u*
+    if (i == 1) us[c - 1] = U(-1, 0, 0);  // the inflow face travels with u*
+}
+
+// The fused predictor: reads u^n (after velnw, interior faces only) and
+// the inflow profile, writes u* to the other buffer set, nu_t of the
+// interior, and updates F_old and the Goldstein integrals in place.
+// Plane step k loads velocity plane k+2 into the slot of plane k-3 (its
+// last reader, the predictor of plane k-2, finished before the previous
+// step's barriers), forms nu_t of plane k+1 in the slot of plane k-2 (last
+// read by the predictor of plane k-1, before this step's first barrier)
+// and predicts plane k.
+// grid (ceil(nx / LT_X), ceil(ny / LT_Y), ceil(nz / LT_KZ)), block LT_THREADS.
+__global__ void __launch_bounds__(LT_THREADS)
+les_predict_tile_kernel(LDev q, int first, const float *__restrict__ u, const float *__restrict__ v,
+                        const float *__restrict__ w, const float *__restrict__ uin,
+                        const uint8_t *__restrict__ face, float *__restrict__ nut, float *__restrict__ us,
+                        float *__restrict__ vs, float *__restrict__ ws, float *__restrict__ fuo,
+                        float *__restrict__ fvo, float *__restrict__ fwo, float *__restrict__ gu,
+                        float *__restrict__ gv, float *__restrict__ gw)
+{
+    __shared__ LesTileSmem sm;
+    const PDims &d = q.d;
+    const int i0 = blockIdx.x * LT_X, j0 = blockIdx.y * LT_Y, k0 = blockIdx.z * LT_KZ;
+    const int k1 = min(k0 + LT_KZ, d.nz);  // planes k0+1 .. k1 are predicted here
+    const int tx = threadIdx.x % LT_X, ty = threadIdx.x / LT_X;
+    const int i = i0 + 1 + tx, j = j0 + 1 + ty;
+    const bool own = i <= d.nx && j <= d.ny;
+    const int o = (ty + 2) * LT_HX + tx + 2;  // the cell in a velocity plane
+    const int on = (ty + 1) * LT_EX + tx + 1;  // and in a nu_t plane
+    const LtMap m = lt_map(d, i0, j0);
+    // prologue: velocity planes k0-1 .. k0+2, nu_t planes k0 and k0+1
+    for (int kk = k0 - 1; kk <= k0 + 2; ++kk) lt_load_plane(q, sm, m, kk, u, v, w, uin);
+    __syncthreads();
+    lt_nut_plane(q, sm, m, k0, false, nut);
+    lt_nut_plane(q, sm, m, k0 + 1, true, nut);
+    for (int k = k0 + 1; k <= k1; ++k) {
+        lt_load_plane(q, sm, m, k + 2, u, v, w, uin);
+        __syncthreads();
+        lt_nut_plane(q, sm, m, k + 1, k + 1 <= k1, nut);
+        __syncthreads();
+        if (own) lt_predict_cell(q, sm, k, i, j, o, on, first != 0, face, us, vs, ws, fuo, fvo, fwo, gu, gv, gw);
+    }
 }
 
 // b = div(u*) / dt at interior cells.
@@ -275,7 +380,8 @@ __global__ void les_rhs_kernel(LDev q, const float *__restrict__ u, const float 
     if (i > d.nx) return;
     const long long c = L(d, i, j, k);
     const float vs = v[L(d, i, (j > 1) ? j - 1 : d.ny, k)];
-    b[c] = q.rdxdt * ((u[c] - u[c - 1]) + (v[c] - vs) + (w[c] - w[c - d.plane]));
+    const float wb = k > 1 ? w[c - d.plane] : 0.0f;  // the ground face is closed
+    b[c] = q.rdxdt * ((u[c] - u[c - 1]) + (v[c] - vs) + (w[c] - wb));
 }
 
 }  // namespace
@@ -360,13 +466,10 @@ gbsw_status les_predictor(gbsw_les *s)
     float *u = s->U[a], *v = s->V[a], *w = s->W[a];
     const dim3 g1(ceil_div(d.nx, 128), d.ny, d.nz), b1(128);
     les_velnw_kernel<<<g1, b1, 0, s->stream>>>(q, s->solver.p_hi, u, v, w);
-    les_bc_x_kernel<<<dim3(ceil_div(d.ny, 128), d.nz), 128, 0, s->stream>>>(q, s->uin, u, v, w);
-    les_bc_y_kernel<<<dim3(ceil_div(d.nx + 2, 128), d.nz), 128, 0, s->stream>>>(q, u, v, w);
-    les_bc_z_kernel<<<dim3(ceil_div(d.nx + 2, 128), d.ny + 2), 128, 0, s->stream>>>(q, u, v, w);
-    les_nut_kernel<<<dim3(ceil_div(d.nx + 2, 64), d.ny + 2, d.nz + 2), 64, 0, s->stream>>>(q, u, v, w, s->nut);
-    les_predict_kernel<<<dim3(ceil_div(d.nx, 32), ceil_div(d.ny, 4), d.nz), dim3(32, 4), 0, s->stream>>>(
-        q, s->step == 0, u, v, w, s->nut, s->face, s->U[bset], s->V[bset], s->W[bset], s->fuo, s->fvo, s->fwo,
-        s->gu, s->gv, s->gw);
+    const dim3 gt(ceil_div(d.nx, LT_X), ceil_div(d.ny, LT_Y), ceil_div(d.nz, LT_KZ));
+    les_predict_tile_kernel<<<gt, LT_THREADS, 0, s->stream>>>(q, s->step == 0, u, v, w, s->uin, s->face, s->nut,
+                                                              s->U[bset], s->V[bset], s->W[bset], s->fuo, s->fvo,
+                                                              s->fwo, s->gu, s->gv, s->gw);
     les_rhs_kernel<<<g1, b1, 0, s->stream>>>(q, s->U[bset], s->V[bset], s->W[bset], s->b);
     GBSW_LAUNCH_CHECK();
     s->cur = bset;
