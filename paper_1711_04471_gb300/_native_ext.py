@@ -31,6 +31,7 @@ def declare(L, sig):
     sig(L, "les_get_step", C.c_int, [vp, ip])
     sig(L, "les_set_step", C.c_int, [vp, C.c_int])
     sig(L, "les_set_solver", C.c_int, [vp, C.c_double, C.c_double, C.c_int, C.c_int])
+    sig(L, "les_set_check_prediction", C.c_int, [vp, C.c_int])
     sig(L, "les_set_fixed_iterations", C.c_int, [vp, C.c_int])
     sig(L, "les_destroy", None, [vp])
     sp = C.POINTER(C.c_double)

@@ -521,6 +521,7 @@ gbsw_status les_create(const gbsw_les_params *params, const uint8_t *solid, void
     s->step = 0;
     gbsw_status st = s->solver.init(P.nx, P.ny, P.nz, P.dx, nullptr, s->stream);
     if (st == GBSW_OK) st = s->solver.configure(P.omega, P.tol, P.max_iter, P.check_every);
+    s->solver.set_predicted_checks(true);
     LDev &q = s->q;
     q.d = s->solver.d;
     q.dt = (float)P.dt;
@@ -742,6 +743,13 @@ gbsw_status les_set_warm_start_factor(gbsw_les *s, int f)
 {
     if (!s || f < 0 || (f != 0 && !ws_fits(s, f))) return GBSW_ERR_ARG;
     s->ws_factor = f;
+    return GBSW_OK;
+}
+
+gbsw_status les_set_check_prediction(gbsw_les *s, int on)
+{
+    if (!s) return GBSW_ERR_ARG;
+    s->solver.set_predicted_checks(on != 0);
     return GBSW_OK;
 }
 

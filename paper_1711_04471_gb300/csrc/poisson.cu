@@ -2,7 +2,9 @@
 // with an FP64 residual norm and a device-side convergence test: one solve
 // is one launch of a CUDA graph whose while-node repeats
 // [m SOR iterations, fold, FP64 residual, test] until ||b - A p|| <= tol ||b||
-// or max_iter, with no host round trip.
+// or max_iter, with no host round trip.  With predicted checks (the UFLES
+// step) the body is a chunk of iterations followed by a check node that
+// runs only when the convergence rate puts the tolerance within reach.
 //
 // FP64 runs at a small fraction of the FP32 rate on this GPU, so the check
 // is arranged to spend few FP64 operations per cell: the FP32 correction is
@@ -212,10 +214,17 @@ poisson_resid_kernel(PDims d, const float *__restrict__ b, const double *__restr
 // Folds the partials (fixed order), updates the control block and sets the
 // while-node condition: continue while rho > tol and iters < max_iter.
 // The ||b||^2 partials are those of the solve's first residual.
+// m: the check interval; counting: m iterations ran since the previous
+// check (ctl->since of them with predict), added to iters.  predict: the
+// next check is placed (see set_predicted_checks): with rho falling by the
+// factor g per iteration between the last two checks, the tolerance is
+// n = log(tol / rho) / log(g) iterations away, and the next check comes
+// after ceil(1.03 n) + 1 of them (an iteration costs far less than a
+// check, so the margin errs late), at most m and max_iter - iters.
 template <bool GRAPH>
 __global__ void __launch_bounds__(POI_RED_THREADS)
 poisson_test_kernel(const double *__restrict__ partials, int nblocks, PoissonCtl *ctl, double tol, int max_iter,
-                    int m, int counting, cudaGraphConditionalHandle handle)
+                    int m, int counting, int predict, cudaGraphConditionalHandle handle)
 {
     __shared__ double red[POI_RED_THREADS / 32];
     double rr = 0.0, bb = 0.0;
@@ -227,7 +236,7 @@ poisson_test_kernel(const double *__restrict__ partials, int nblocks, PoissonCtl
     bb = block_sum_f64<POI_RED_THREADS / 32>(bb, red);
     if (threadIdx.x == 0) {
         if (counting) {
-            ctl->iters += m;
+            ctl->iters += predict ? ctl->since : m;
         } else {
             ctl->iters = 0;
             ctl->status = DEV_OK;
@@ -240,8 +249,37 @@ poisson_test_kernel(const double *__restrict__ partials, int nblocks, PoissonCtl
         if (bad) ctl->status = DEV_NONFINITE;
         const bool done = bad || bb < 1e-60 || rho <= tol || ctl->iters >= max_iter;
         ctl->done = done ? 1 : 0;
+        int next = m;
+        if (predict && counting && !done && rho > 0.0 && rho < ctl->rho_prev && ctl->iters > ctl->iters_prev) {
+            const double lg = log(rho / ctl->rho_prev) / (double)(ctl->iters - ctl->iters_prev);  // < 0
+            const double n = log(tol / rho) / lg;                                                // > 0
+            if (n < (double)m) next = max(1, (int)ceil(1.03 * n) + 1);
+        }
+        ctl->next = max(1, min(next, max_iter - ctl->iters));
+        ctl->since = 0;
+        ctl->rho_prev = rho;
+        ctl->iters_prev = ctl->iters;
         if (GRAPH) cudaGraphSetConditional(handle, done ? 0u : 1u);
     }
+}
+
+// Predicted checks, after each chunk of c iterations of the loop body:
+// counts them and sets the condition of the check node (a check is due
+// once the iterations since the last one reach ctl->next, or max_iter).
+__global__ void poisson_due_kernel(PoissonCtl *ctl, int c, int max_iter, cudaGraphConditionalHandle check)
+{
+    if (threadIdx.x != 0) return;
+    const int since = ctl->since + c;
+    ctl->since = since;
+    const bool due = since >= ctl->next || ctl->iters + since >= max_iter;
+    cudaGraphSetConditional(check, due ? 1u : 0u);
+}
+
+// Predicted checks, end of the loop body: continue unless the last check
+// found the solve done.
+__global__ void poisson_continue_kernel(const PoissonCtl *ctl, cudaGraphConditionalHandle loop)
+{
+    if (threadIdx.x == 0) cudaGraphSetConditional(loop, ctl->done ? 0u : 1u);
 }
 
 // p_hi += e, e = 0 on the interior cells of one colour (before each check).
@@ -317,17 +355,18 @@ static cudaError_t launch_sweep(const PDims &d, int colour, float om, float h2, 
     return cudaLaunchKernelEx(&cfg, sor_sweep_kernel<FIRST, false>, d, colour, om, h2, dg, ec, eo, rc);
 }
 
-// m red-black iterations, the first from e = 0 (FIRST).
+// m red-black iterations; with from_zero the first starts from e = 0
+// (FIRST: its red half-sweep reads no neighbours).
 static cudaError_t launch_iterations(const PDims &d, int m, float om, float h2, float *const e[2],
-                                     float *const r[2], cudaStream_t s)
+                                     float *const r[2], cudaStream_t s, bool from_zero = true)
 {
     cudaError_t err = cudaSuccess;
     for (int it = 0; it < m && err == cudaSuccess; ++it) {
-        if (it == 0) {
+        if (it == 0 && from_zero) {
             err = launch_sweep<true>(d, 0, om, h2, e[0], e[1], r[0], s, false);
             if (err == cudaSuccess) err = launch_sweep<true>(d, 1, om, h2, e[1], e[0], r[1], s, true);
         } else {
-            err = launch_sweep<false>(d, 0, om, h2, e[0], e[1], r[0], s, true);
+            err = launch_sweep<false>(d, 0, om, h2, e[0], e[1], r[0], s, it > 0);
             if (err == cudaSuccess) err = launch_sweep<false>(d, 1, om, h2, e[1], e[0], r[1], s, true);
         }
     }
@@ -400,8 +439,15 @@ gbsw_status PoissonSolver::configure(double omega_, double tol_, int max_iter_, 
     return GBSW_OK;
 }
 
+void PoissonSolver::set_predicted_checks(bool on)
+{
+    if (on != predict_) dirty_ = true;
+    predict_ = on;
+}
+
 gbsw_status PoissonSolver::build_graph()
 {
+    if (predict_) return build_graph_predicted();
     if (exec_) cudaGraphExecDestroy(exec_);
     if (graph_) cudaGraphDestroy(graph_);
     exec_ = nullptr;
@@ -432,7 +478,7 @@ gbsw_status PoissonSolver::build_graph()
         poisson_resid_kernel<true><<<rgrid, POI_RED_THREADS, 0, cs>>>(d, b, p_hi, r[0], r[1], partials);
         chk(cudaGetLastError());
         poisson_test_kernel<true><<<1, POI_RED_THREADS, 0, cs>>>(partials, rblocks, ctl, tol, max_iter, m, 0,
-                                                                  handle);
+                                                                  0, handle);
         chk(cudaGetLastError());
         // while node
         cudaStreamCaptureStatus cst;
@@ -461,7 +507,7 @@ gbsw_status PoissonSolver::build_graph()
             poisson_fold_kernel<<<fgrid, fblock, 0, cs>>>(d, 1, p_hi, e[1]);
             poisson_resid_kernel<false><<<rgrid, POI_RED_THREADS, 0, cs>>>(d, b, p_hi, r[0], r[1], partials);
             poisson_test_kernel<true><<<1, POI_RED_THREADS, 0, cs>>>(partials, rblocks, ctl, tol, max_iter, m,
-                                                                    1, handle);
+                                                                    1, 0, handle);
             chk(cudaGetLastError());
         }
         cudaGraph_t body_out = nullptr;
@@ -471,6 +517,114 @@ gbsw_status PoissonSolver::build_graph()
     cudaStreamDestroy(cs);
     if (err != cudaSuccess) {
         record_cuda_error(err, "poisson graph build", __FILE__, __LINE__);
+        return GBSW_ERR_CUDA;
+    }
+    dirty_ = false;
+    return GBSW_OK;
+}
+
+// The solve graph with predicted checks: prelude (e = 0, first residual,
+// test), then a while node whose body is a chunk of c iterations (c the
+// largest divisor of m up to SOR_CHUNK_MAX), poisson_due_kernel, an if
+// node holding the check (fold, FP64 residual, test with prediction) and
+// poisson_continue_kernel.  Every chunk starts from the correction as the
+// last chunk or check left it; after a check it is 0, where the general
+// red half-sweep gives bitwise what the FIRST one does.
+gbsw_status PoissonSolver::build_graph_predicted()
+{
+    if (exec_) cudaGraphExecDestroy(exec_);
+    if (graph_) cudaGraphDestroy(graph_);
+    exec_ = nullptr;
+    graph_ = nullptr;
+
+    int c = 1;
+    for (int x = std::min(m, SOR_CHUNK_MAX); x >= 1; --x)
+        if (m % x == 0) {
+            c = x;
+            break;
+        }
+    const size_t nc = (size_t)d.cplane * (size_t)(d.nz + 2);
+    const float om = (float)omega, h2 = (float)(d.dx * d.dx);
+    const int nxh = (d.nx + 1) / 2;
+    const dim3 fgrid(ceil_div(nxh, 128), d.ny, d.nz), fblock(128);
+
+    cudaStream_t cs = nullptr;
+    GBSW_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaError_t err = cudaSuccess;
+    auto chk = [&](cudaError_t e2) {
+        if (err == cudaSuccess && e2 != cudaSuccess) err = e2;
+    };
+    // Add a conditional node of the given type at the current capture
+    // point of cs and make it the capture's only dependency; its body graph
+    // goes to *body.
+    auto add_conditional = [&](cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type, cudaGraph_t *body) {
+        cudaStreamCaptureStatus cst;
+        cudaGraph_t cap_graph;
+        const cudaGraphNode_t *deps = nullptr;
+        size_t ndeps = 0;
+        chk(cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cap_graph, &deps, nullptr, &ndeps));
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = type;
+        cp.conditional.size = 1;
+        cudaGraphNode_t node;
+        if (err == cudaSuccess) chk(cudaGraphAddNode(&node, cap_graph, deps, nullptr, ndeps, &cp));
+        if (err == cudaSuccess)
+            chk(cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+        *body = err == cudaSuccess ? cp.conditional.phGraph_out[0] : nullptr;
+    };
+    cudaGraphConditionalHandle hloop = 0, hcheck = 0;
+    cudaGraph_t body = nullptr, check_body = nullptr;
+    chk(cudaGraphCreate(&graph_, 0));
+    chk(cudaGraphConditionalHandleCreate(&hloop, graph_, 0, cudaGraphCondAssignDefault));
+    chk(cudaStreamBeginCaptureToGraph(cs, graph_, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    if (err == cudaSuccess) {
+        // prelude: e = 0, r = b - A p_hi, ||b||^2, first test (next = m)
+        chk(cudaMemsetAsync(e[0], 0, nc * sizeof(float), cs));
+        chk(cudaMemsetAsync(e[1], 0, nc * sizeof(float), cs));
+        poisson_resid_kernel<true><<<rgrid, POI_RED_THREADS, 0, cs>>>(d, b, p_hi, r[0], r[1], partials);
+        chk(cudaGetLastError());
+        poisson_test_kernel<true><<<1, POI_RED_THREADS, 0, cs>>>(partials, rblocks, ctl, tol, max_iter, m, 0, 1,
+                                                                  hloop);
+        chk(cudaGetLastError());
+        add_conditional(hloop, cudaGraphCondTypeWhile, &body);
+    }
+    cudaGraph_t captured = nullptr;
+    chk(cudaStreamEndCapture(cs, &captured));
+    if (err == cudaSuccess) {
+        // loop body: c iterations, due test, check node, loop condition
+        chk(cudaGraphConditionalHandleCreate(&hcheck, body, 0, cudaGraphCondAssignDefault));
+        chk(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        if (err == cudaSuccess) {
+            chk(launch_iterations(d, c, om, h2, e, r, cs, false));
+            poisson_due_kernel<<<1, 32, 0, cs>>>(ctl, c, max_iter, hcheck);
+            chk(cudaGetLastError());
+            add_conditional(hcheck, cudaGraphCondTypeIf, &check_body);
+            poisson_continue_kernel<<<1, 32, 0, cs>>>(ctl, hloop);
+            chk(cudaGetLastError());
+        }
+        cudaGraph_t body_out = nullptr;
+        chk(cudaStreamEndCapture(cs, &body_out));
+    }
+    if (err == cudaSuccess) {
+        // check: fold the correction into p_hi, FP64 residual, test and prediction
+        chk(cudaStreamBeginCaptureToGraph(cs, check_body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        if (err == cudaSuccess) {
+            poisson_fold_kernel<<<fgrid, fblock, 0, cs>>>(d, 0, p_hi, e[0]);
+            poisson_fold_kernel<<<fgrid, fblock, 0, cs>>>(d, 1, p_hi, e[1]);
+            poisson_resid_kernel<false><<<rgrid, POI_RED_THREADS, 0, cs>>>(d, b, p_hi, r[0], r[1], partials);
+            poisson_test_kernel<false><<<1, POI_RED_THREADS, 0, cs>>>(partials, rblocks, ctl, tol, max_iter, m, 1,
+                                                                     1, 0);
+            chk(cudaGetLastError());
+        }
+        cudaGraph_t check_out = nullptr;
+        chk(cudaStreamEndCapture(cs, &check_out));
+    }
+    if (err == cudaSuccess) chk(cudaGraphInstantiate(&exec_, graph_, 0));
+    cudaStreamDestroy(cs);
+    if (err != cudaSuccess) {
+        record_cuda_error(err, "poisson graph build (predicted checks)", __FILE__, __LINE__);
         return GBSW_ERR_CUDA;
     }
     dirty_ = false;
@@ -526,7 +680,7 @@ gbsw_status PoissonSolver::record_fixed(int niter, cudaStream_t stream)
     GBSW_CUDA_TRY(cudaMemsetAsync(e[0], 0, nc * sizeof(float), stream));
     GBSW_CUDA_TRY(cudaMemsetAsync(e[1], 0, nc * sizeof(float), stream));
     poisson_resid_kernel<true><<<rgrid, POI_RED_THREADS, 0, stream>>>(d, b, p_hi, r[0], r[1], partials);
-    poisson_test_kernel<false><<<1, POI_RED_THREADS, 0, stream>>>(partials, rblocks, ctl, 0.0, niter, 0, 0, 0);
+    poisson_test_kernel<false><<<1, POI_RED_THREADS, 0, stream>>>(partials, rblocks, ctl, 0.0, niter, 0, 0, 0, 0);
     cudaError_t err = launch_iterations(d, niter, om, h2, e, r, stream);
     if (err != cudaSuccess) {
         record_cuda_error(err, "SOR sweep launch", __FILE__, __LINE__);
@@ -536,7 +690,7 @@ gbsw_status PoissonSolver::record_fixed(int niter, cudaStream_t stream)
     poisson_fold_kernel<<<fgrid, fblock, 0, stream>>>(d, 1, p_hi, e[1]);
     poisson_resid_kernel<false><<<rgrid, POI_RED_THREADS, 0, stream>>>(d, b, p_hi, r[0], r[1], partials);
     poisson_test_kernel<false><<<1, POI_RED_THREADS, 0, stream>>>(partials, rblocks, ctl, 0.0, niter, niter,
-                                                                   1, 0);
+                                                                   1, 0, 0);
     GBSW_LAUNCH_CHECK();
     return GBSW_OK;
 }

@@ -49,7 +49,10 @@ struct PoissonCtl {
     int iters;        // SOR iterations done
     int done;
     int status;       // DEV_* code
-    int pad;
+    int next;         // predicted checks: iterations from the last check to the next
+    double rho_prev;  // predicted checks: rho and iters at the check before the last
+    int iters_prev;
+    int since;        // predicted checks: iterations since the last check
 };
 
 class PoissonSolver {
@@ -59,6 +62,14 @@ public:
     gbsw_status init(int nx, int ny, int nz, double dx, const float *b, cudaStream_t stream);
     void release();
     gbsw_status configure(double omega, double tol, int max_iter, int check_every);
+    // Predicted checks: after a check, the next one comes at the iteration
+    // where the convergence rate measured between the last two checks
+    // reaches the tolerance (with a small margin), rounded up to a whole
+    // chunk of the loop body (the largest divisor of check_every up to
+    // SOR_CHUNK_MAX), and never later than check_every iterations.  The
+    // iterates and the stopping test are unchanged; only where the test is
+    // taken moves.  Off: a test every check_every iterations.
+    void set_predicted_checks(bool on);
     // Enqueue one solve (asynchronous; one graph launch).
     gbsw_status enqueue();
     // Enqueue exactly niter iterations with no convergence test (the
@@ -85,6 +96,7 @@ public:
 
 private:
     gbsw_status build_graph();
+    gbsw_status build_graph_predicted();
     gbsw_status record_fixed(int niter, cudaStream_t s);
     cudaGraphExec_t fixed_exec_ = nullptr;
     int fixed_niter_ = -1;
@@ -92,6 +104,7 @@ private:
     cudaGraph_t graph_ = nullptr;
     cudaGraphExec_t exec_ = nullptr;
     bool dirty_ = true;
+    bool predict_ = false;
 };
 
 constexpr int POI_RES_PLANES = 16;    // z-planes per thread of the residual kernel
@@ -99,6 +112,7 @@ constexpr int SOR_SLOT0 = 4;          // offset of slot 0 in a colour row (keeps
 constexpr int SOR_THREADS = 128;      // threads per block of the SOR sweep
 constexpr int SOR_KZ = 2;             // z-planes per thread of the SOR sweep
 constexpr int SOR_FIXED_GRAPH_MAX_ITER = 1000;   // longest fixed-count solve captured into a graph
+constexpr int SOR_CHUNK_MAX = 50;     // predicted checks: iterations per loop body at most
 constexpr int POI_RED_THREADS = 256;
 
 // The values 4, 5, 6, 7 that the diagonal d_c takes, and their reciprocals

@@ -100,6 +100,11 @@ class LES:
         p.check_every = p.check_every if check_every is None else int(check_every)
         N.check(N.lib().les_set_solver(self._h, p.omega, p.tol, p.max_iter, p.check_every), "les_set_solver")
 
+    def set_check_prediction(self, on: bool):
+        """Predicted convergence checks (on by default): see
+        les_set_check_prediction in include/gbsw.h."""
+        N.check(N.lib().les_set_check_prediction(self._h, int(bool(on))), "les_set_check_prediction")
+
     def set_warm_start(self, net, factor: int = 0):
         """Use a UNet (paper_1711_04471_gb300.unet.UNet) as the pressure warm
         start, run on the grid coarsened by `factor` (0: the default, 16 on
