@@ -140,26 +140,29 @@ __device__ __forceinline__ LtMap lt_map(const PDims &d, int i0, int j0)
     return m;
 }
 
-// Velocity plane kk (0 .. nz+1) of the tile after bondv1, into its slot:
-// ground ghost reflected u, v; lid ghost copied u, v; w = 0 on both and on
-// the lid face; inflow profile and reflected v, w at i = 0.
-__device__ __forceinline__ void lt_load_plane(const LDev &q, LesTileSmem &sm, const LtMap &m, int kk,
-                                              const float *__restrict__ u, const float *__restrict__ v,
-                                              const float *__restrict__ w, const float *__restrict__ uin)
+struct LtVel {
+    float u[LT_LPT], v[LT_LPT], w[LT_LPT];
+};
+
+// Global reads of velocity plane kk after bondv1, into registers (zeros
+// for a plane outside 0 .. nz+1, which no stage reads): ground ghost
+// reflected u, v; lid ghost copied u, v; w = 0 on both and on the lid
+// face; inflow profile and reflected v, w at i = 0.
+__device__ __forceinline__ LtVel lt_fetch_plane(const LDev &q, const LtMap &m, int kk, const float *__restrict__ u,
+                                                const float *__restrict__ v, const float *__restrict__ w,
+                                                const float *__restrict__ uin)
 {
     const PDims &d = q.d;
-    if (kk < 0 || kk > d.nz + 1) return;
-    float *pu = sm.vel[lt_uslot(kk)][0], *pv = sm.vel[lt_uslot(kk)][1], *pw = sm.vel[lt_uslot(kk)][2];
-    const int kc = kk == 0 ? 1 : (kk == d.nz + 1 ? d.nz : kk);
+    LtVel r;
+    const bool ok = kk >= 0 && kk <= d.nz + 1;
+    const int kc = kk <= 0 ? 1 : (kk >= d.nz + 1 ? d.nz : kk);
     const bool ground = kk == 0, wzero = kk == 0 || kk >= d.nz;
     const long long base = (long long)kc * d.plane;
-    const float uin_k = uin[kc];
+    const float uin_k = ok ? uin[kc] : 0.0f;
 #pragma unroll
     for (int c = 0; c < LT_LPT; ++c) {
-        const int idx = threadIdx.x + c * LT_THREADS;
-        if (idx >= LT_HN) continue;
         float a = 0.0f, b = 0.0f, cw = 0.0f;
-        if (m.src[c] >= 0) {
+        if (ok && m.src[c] >= 0) {
             const long long cc = base + m.src[c];
             const bool in = (m.inflow >> c) & 1u;
             const float uu = in ? uin_k : u[cc];
@@ -172,9 +175,23 @@ __device__ __forceinline__ void lt_load_plane(const LDev &q, LesTileSmem &sm, co
             b = ground ? -vv : vv;
             cw = wzero ? 0.0f : ww;
         }
-        pu[idx] = a;
-        pv[idx] = b;
-        pw[idx] = cw;
+        r.u[c] = a;
+        r.v[c] = b;
+        r.w[c] = cw;
+    }
+    return r;
+}
+
+__device__ __forceinline__ void lt_store_plane(LesTileSmem &sm, const LtVel &r, int kk)
+{
+    float *pu = sm.vel[lt_uslot(kk)][0], *pv = sm.vel[lt_uslot(kk)][1], *pw = sm.vel[lt_uslot(kk)][2];
+#pragma unroll
+    for (int c = 0; c < LT_LPT; ++c) {
+        const int idx = threadIdx.x + c * LT_THREADS;
+        if (idx >= LT_HN) continue;
+        pu[idx] = r.u[c];
+        pv[idx] = r.v[c];
+        pw[idx] = r.w[c];
     }
 }
 
@@ -232,9 +249,12 @@ __device__ __forceinline__ void lt_nut_plane(const LDev &q, LesTileSmem &sm, con
 
 // velfg + feedbf + viscous terms + adam on the three faces owned by the
 // thread's cell (i, j, k) of plane k, from the velocity and nu_t rings.
+// fl, fuo_c, fvo_c, fwo_c: the cell's face flags and F_old, read by the
+// caller before the plane step's barriers (their latency hides behind the
+// load and nu_t stages).
 __device__ __forceinline__ void lt_predict_cell(const LDev &q, const LesTileSmem &sm, int k, int i, int j, int o,
-                                                int on, bool first, const uint8_t *__restrict__ face,
-                                                float *__restrict__ us, float *__restrict__ vs,
+                                                int on, bool first, uint8_t fl, float fuo_c, float fvo_c,
+                                                float fwo_c, float *__restrict__ us, float *__restrict__ vs,
                                                 float *__restrict__ ws, float *__restrict__ fuo,
                                                 float *__restrict__ fvo, float *__restrict__ fwo,
                                                 float *__restrict__ gu, float *__restrict__ gv, float *__restrict__ gw)
@@ -269,7 +289,6 @@ __device__ __forceinline__ void lt_predict_cell(const LDev &q, const LesTileSmem
         return 2.0f * ne * s;
     };
     const long long c = L(d, i, j, k);
-    const uint8_t fl = face[c];
     const float dt = q.dt;
     const float t12 = T12(0, 0, 0), t13 = T13(0, 0, 0), t23 = T23(0, 0, 0);
     // ---- u face (i+1/2, j, k)
@@ -286,7 +305,7 @@ __device__ __forceinline__ void lt_predict_cell(const LDev &q, const LesTileSmem
             f += q.alpha * g + q.beta * U(0, 0, 0);
         }
         f += r * ((T11(1, 0, 0) - T11(0, 0, 0)) + (t12 - T12(0, -1, 0)) + (t13 - T13(0, 0, -1)));
-        const float fo = fuo[c];
+        const float fo = fuo_c;
         us[c] = U(0, 0, 0) + dt * (first ? f : 1.5f * f - 0.5f * fo);
         fuo[c] = f;
     }
@@ -304,7 +323,7 @@ __device__ __forceinline__ void lt_predict_cell(const LDev &q, const LesTileSmem
             f += q.alpha * g + q.beta * V(0, 0, 0);
         }
         f += r * ((t12 - T12(-1, 0, 0)) + (T22(0, 1, 0) - T22(0, 0, 0)) + (t23 - T23(0, 0, -1)));
-        const float fo = fvo[c];
+        const float fo = fvo_c;
         vs[c] = V(0, 0, 0) + dt * (first ? f : 1.5f * f - 0.5f * fo);
         fvo[c] = f;
     }
@@ -322,7 +341,7 @@ __device__ __forceinline__ void lt_predict_cell(const LDev &q, const LesTileSmem
             f += q.alpha * g + q.beta * W(0, 0, 0);
         }
         f += r * ((t13 - T13(-1, 0, 0)) + (t23 - T23(0, -1, 0)) + (T33(0, 0, 1) - T33(0, 0, 0)));
-        const float fo = fwo[c];
+        const float fo = fwo_c;
         ws[c] = W(0, 0, 0) + dt * (first ? f : 1.5f * f - 0.5f * fo);
         fwo[c] = f;
     }
@@ -332,11 +351,14 @@ __device__ __forceinline__ void lt_predict_cell(const LDev &q, const LesTileSmem
 // The fused predictor: reads u^n (after velnw, interior faces only) and
 // the inflow profile, writes u* to the other buffer set, nu_t of the
 // interior, and updates F_old and the Goldstein integrals in place.
-// Plane step k loads velocity plane k+2 into the slot of plane k-3 (its
-// last reader, the predictor of plane k-2, finished before the previous
-// step's barriers), forms nu_t of plane k+1 in the slot of plane k-2 (last
-// read by the predictor of plane k-1, before this step's first barrier)
-// and predicts plane k.
+// Plane step k stores velocity plane k+2 (read from global memory during
+// the previous step) into the slot of plane k-3 (its last reader, the
+// predictor of plane k-2, finished before the previous step's barriers),
+// issues the global reads of plane k+3 and of the step's own face flags and
+// F_old, forms nu_t of plane k+1 in the slot of plane k-2 (last read by the
+// predictor of plane k-1, before this step's first barrier) and predicts
+// plane k: the global reads' latency hides behind the nu_t and predictor
+// stages.
 // grid (ceil(nx / LT_X), ceil(ny / LT_Y), ceil(nz / LT_KZ)), block LT_THREADS.
 __global__ void __launch_bounds__(LT_THREADS)
 les_predict_tile_kernel(LDev q, int first, const float *__restrict__ u, const float *__restrict__ v,
@@ -357,16 +379,29 @@ les_predict_tile_kernel(LDev q, int first, const float *__restrict__ u, const fl
     const int on = (ty + 1) * LT_EX + tx + 1;  // and in a nu_t plane
     const LtMap m = lt_map(d, i0, j0);
     // prologue: velocity planes k0-1 .. k0+2, nu_t planes k0 and k0+1
-    for (int kk = k0 - 1; kk <= k0 + 2; ++kk) lt_load_plane(q, sm, m, kk, u, v, w, uin);
+    for (int kk = k0 - 1; kk <= k0 + 2; ++kk) lt_store_plane(sm, lt_fetch_plane(q, m, kk, u, v, w, uin), kk);
+    LtVel ahead = lt_fetch_plane(q, m, k0 + 3, u, v, w, uin);
     __syncthreads();
     lt_nut_plane(q, sm, m, k0, false, nut);
     lt_nut_plane(q, sm, m, k0 + 1, true, nut);
     for (int k = k0 + 1; k <= k1; ++k) {
-        lt_load_plane(q, sm, m, k + 2, u, v, w, uin);
+        uint8_t fl = 0;
+        float fuo_c = 0.0f, fvo_c = 0.0f, fwo_c = 0.0f;
+        if (own) {  // the predictor's own global reads, issued first
+            const long long c = L(d, i, j, k);
+            fl = face[c];
+            fuo_c = fuo[c];
+            fvo_c = fvo[c];
+            fwo_c = fwo[c];
+        }
+        lt_store_plane(sm, ahead, k + 2);
         __syncthreads();
+        if (k + 1 <= k1) ahead = lt_fetch_plane(q, m, k + 3, u, v, w, uin);  // consumed by the next plane step
         lt_nut_plane(q, sm, m, k + 1, k + 1 <= k1, nut);
         __syncthreads();
-        if (own) lt_predict_cell(q, sm, k, i, j, o, on, first != 0, face, us, vs, ws, fuo, fvo, fwo, gu, gv, gw);
+        if (own)
+            lt_predict_cell(q, sm, k, i, j, o, on, first != 0, fl, fuo_c, fvo_c, fwo_c, us, vs, ws, fuo, fvo, fwo, gu,
+                            gv, gw);
     }
 }
 

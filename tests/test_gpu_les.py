@@ -173,6 +173,34 @@ def test_single_step_from_identical_state(G, warm):
     assert it_o - 1 <= stats[0]["iters"] < it_o + 6
 
 
+def test_predicted_checks_keep_the_stopping_rule(G):
+    """Predicted convergence checks (the default of an LES context): with
+    check_every = 100 the solve loop runs chunks of 50 iterations and checks
+    where the measured convergence rate puts the tolerance, at most 100
+    iterations after the previous check.  Both variants stop at a check
+    whose FP64 residual is within tol: the fixed interval at the first
+    multiple of 100 past the oracle's count, the predicted one at a multiple
+    of 50 within one interval of it; the pressure matches the oracle."""
+    nx, ny, nz, solid = small_case()
+    P = ol.make_params(nx, ny, nz, tol=1e-9)
+    s = ol.LESState(P, solid).step(3)
+    got = {}
+    for predicted in (False, True):
+        with _gpu_from_oracle(G, s, nx, ny, nz, solid, tol=1e-9, check_every=100) as g:
+            if not predicted:
+                g.set_check_prediction(False)
+            st = g.step(1)[0]
+            got[predicted] = (st, g.get("p"))
+    s.step(1)
+    it_o = s.history[-1][0]
+    off, on = got[False][0], got[True][0]
+    assert off["status"] == on["status"] == 0 and off["rel_res"] <= 1e-9 and on["rel_res"] <= 1e-9
+    assert off["iters"] % 100 == 0 and it_o - 1 <= off["iters"] < it_o + 100, (off["iters"], it_o)
+    assert on["iters"] % 50 == 0 and it_o - 1 <= on["iters"] < it_o + 100, (on["iters"], it_o)
+    for predicted in (False, True):
+        assert rel_l2(got[predicted][1], s.p, INT) <= REL, predicted
+
+
 def test_ten_step_horizon_and_iteration_counts(G):
     nx, ny, nz, solid = small_case(40, 32, 20, seed=9)
     P = ol.make_params(nx, ny, nz)
