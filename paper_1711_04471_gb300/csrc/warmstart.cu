@@ -52,12 +52,51 @@ __device__ __forceinline__ double ws_weight(int i, int I, int nc, double inv, in
     return I == nc - 1 ? (rule == 2 ? 1.0 - 2.0 * w : 1.0) : 0.0;
 }
 
-// Full weighting, pass x: ar/ap (nz, ny, ncx) = weighted sums along x of
-// r = b - A p (formed here) and of p.  Coarse I draws on the 2f fine cells
-// [I f - f/2, I f + 3f/2) (clipped); the sums run in a fixed order.
+// The residual r = b - A p of every fine cell, in FP64, once (the x pass
+// reads it for both coarse cells a fine cell feeds).  r2 = 1/dx^2 from the
+// host; the diagonal 6 - [i == 1] - [k == 1] - [k == nz] + [i == nx] is
+// picked by integer selects (no FP64 operation).  r: dense (nz, ny, nx).
 __global__ void __launch_bounds__(WS_THREADS)
-ws_fw_x_kernel(const float *__restrict__ b, const double *__restrict__ p, WsGrid g, double dx, int f,
-               double *__restrict__ ar, double *__restrict__ ap)
+ws_resid_kernel(const float *__restrict__ b, const double *__restrict__ p, WsGrid g, double r2,
+                double *__restrict__ r)
+{
+    const long long n = (long long)g.nx * g.ny * g.nz;
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const int i = (int)(q % g.nx) + 1;
+    const int j = (int)((q / g.nx) % g.ny) + 1;
+    const int k = (int)(q / ((long long)g.nx * g.ny)) + 1;
+    const int jm = j == 1 ? g.ny : j - 1, jp = j == g.ny ? 1 : j + 1;
+    auto P = [&](int ii, int jj, int kk) -> double {
+        if (ii < 1 || ii > g.nx || kk < 1 || kk > g.nz) return 0.0;
+        return p[ws_at(g, ii, jj, kk)];
+    };
+    const int dci = 6 - (i == 1) - (k == 1) - (k == g.nz) + (i == g.nx);
+    const double diag = dci == 6 ? 6.0 : (dci == 5 ? 5.0 : (dci == 7 ? 7.0 : (dci == 4 ? 4.0 : 3.0)));
+    const double pv = P(i, j, k);
+    const double nb = (P(i - 1, j, k) + P(i + 1, j, k)) + (P(i, jm, k) + P(i, jp, k)) +
+                      (P(i, j, k - 1) + P(i, j, k + 1));
+    r[q] = (double)b[ws_at(g, i, j, k)] - (nb - diag * pv) * r2;
+}
+
+// Table of the full-weighting weights along one axis of n fine cells and
+// nc = n / f coarse cells: entry I * 2f + o is the weight of fine cell
+// I f - f/2 + o in coarse cell I (0 outside the axis), by ws_weight.
+__global__ void ws_wtab_kernel(int n, int nc, int f, int rule, double *__restrict__ wtab)
+{
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nc * 2 * f) return;
+    const int I = idx / (2 * f), i0 = I * f - f / 2 + idx % (2 * f);
+    wtab[idx] = (i0 >= 0 && i0 < n) ? ws_weight(i0, I, nc, 1.0 / f, rule) : 0.0;
+}
+
+// Full weighting, pass x: ar/ap (nz, ny, ncx) = weighted sums along x of
+// the residual r (dense, from ws_resid_kernel) and of p.  Coarse I draws on
+// the 2f fine cells [I f - f/2, I f + 3f/2) (clipped); the sums run in a
+// fixed order, with the weights of ws_wtab_kernel (rule 2).
+__global__ void __launch_bounds__(WS_THREADS)
+ws_fw_x_kernel(const double *__restrict__ r, const double *__restrict__ p, WsGrid g, int f,
+               const double *__restrict__ wtab, double *__restrict__ ar, double *__restrict__ ap)
 {
     const int ncx = g.nx / f;
     const long long n = (long long)g.nz * g.ny * ncx;
@@ -66,24 +105,15 @@ ws_fw_x_kernel(const float *__restrict__ b, const double *__restrict__ p, WsGrid
     const int I = (int)(q % ncx);
     const int j = (int)((q / ncx) % g.ny) + 1;
     const int k = (int)(q / ((long long)ncx * g.ny)) + 1;
-    const int jm = j == 1 ? g.ny : j - 1, jp = j == g.ny ? 1 : j + 1;
-    const double r2 = 1.0 / (dx * dx), inv = 1.0 / f;
-    auto P = [&](int ii, int jj, int kk) -> double {
-        if (ii < 1 || ii > g.nx || kk < 1 || kk > g.nz) return 0.0;
-        return p[ws_at(g, ii, jj, kk)];
-    };
+    const long long row = ((long long)(k - 1) * g.ny + (j - 1)) * g.nx;
     double sr = 0.0, sp = 0.0;
-    const int lo = max(I * f - f / 2, 0), hi = min(I * f + (3 * f) / 2, g.nx);
+    const int base = I * f - f / 2;
+    const int lo = max(base, 0), hi = min(I * f + (3 * f) / 2, g.nx);
     for (int i0 = lo; i0 < hi; ++i0) {
-        const double w = ws_weight(i0, I, ncx, inv, 2);
+        const double w = wtab[I * 2 * f + (i0 - base)];
         if (w == 0.0) continue;
-        const int i = i0 + 1;
-        const double diag = 6.0 - (i == 1) - (k == 1) - (k == g.nz) + (i == g.nx);
-        const double pv = P(i, j, k);
-        const double nb = (P(i - 1, j, k) + P(i + 1, j, k)) + (P(i, jm, k) + P(i, jp, k)) +
-                          (P(i, j, k - 1) + P(i, j, k + 1));
-        sr += w * ((double)b[ws_at(g, i, j, k)] - (nb - diag * pv) * r2);
-        sp += w * pv;
+        sr += w * r[row + i0];
+        sp += w * p[ws_at(g, i0 + 1, j, k)];
     }
     ar[q] = sr;
     ap[q] = sp;
@@ -165,15 +195,23 @@ ws_prepare_kernel(const double *__restrict__ rc, const double *__restrict__ pc, 
     }
 }
 
+// p += s * prolong(out) on the fine cells of column (i, j), planes
+// WS_KCH c .. WS_KCH c + WS_KCH - 1 (one thread).  The x and y
+// interpolation of the two coarse planes k0, k1 (c0, c1) is formed again
+// only when they change along the column; each cell then takes the z
+// interpolation, the same expressions in the same order as a cell-by-cell
+// evaluation.
+constexpr int WS_KCH = 8;
 __global__ void __launch_bounds__(WS_THREADS)
 ws_prolong_kernel(const float *__restrict__ out, WsGrid g, int f, const double *__restrict__ scale,
                   double *__restrict__ p)
 {
-    const long long n = (long long)g.nx * g.ny * g.nz;
+    const int nch = (g.nz + WS_KCH - 1) / WS_KCH;
+    const long long n = (long long)g.nx * g.ny * nch;
     const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= n) return;
     const double s = *scale;
-    const int i = (int)(v % g.nx), j = (int)((v / g.nx) % g.ny), k = (int)(v / ((long long)g.nx * g.ny));
+    const int i = (int)(v % g.nx), j = (int)((v / g.nx) % g.ny), ch = (int)(v / ((long long)g.nx * g.ny));
     const int ncx = g.nx / f, ncy = g.ny / f, ncz = g.nz / f;
     const double inv = 1.0 / f;
     // x: held at the inflow, antisymmetric ghost past the outflow
@@ -191,16 +229,25 @@ ws_prolong_kernel(const float *__restrict__ out, WsGrid g, int f, const double *
     const int jf = (int)floor(Y);
     const double wy = Y - jf;
     const int j0 = (jf + ncy) % ncy, j1 = (jf + 1) % ncy;
-    // z: held at the ground and the lid
-    const double Z = fmin(fmax((k + 0.5) * inv - 0.5, 0.0), ncz - 1.0);
-    const int k0 = min((int)floor(Z), ncz - 1);
-    const double wz = Z - k0;
-    const int k1 = min(k0 + 1, ncz - 1);
     auto C = [&](int kk, int jj, int ii) { return (double)out[((long long)kk * ncy + jj) * ncx + ii]; };
     auto line = [&](int kk, int jj) { return (1.0 - wx) * C(kk, jj, i0) + wx * sx * C(kk, jj, i1); };
-    const double c0 = (1.0 - wy) * line(k0, j0) + wy * line(k0, j1);
-    const double c1 = (1.0 - wy) * line(k1, j0) + wy * line(k1, j1);
-    p[ws_at(g, i + 1, j + 1, k + 1)] += s * ((1.0 - wz) * c0 + wz * c1);
+    int kc0 = -1, kc1 = -1;
+    double c0 = 0.0, c1 = 0.0;
+    const int kend = min((ch + 1) * WS_KCH, g.nz);
+    for (int k = ch * WS_KCH; k < kend; ++k) {
+        // z: held at the ground and the lid
+        const double Z = fmin(fmax((k + 0.5) * inv - 0.5, 0.0), ncz - 1.0);
+        const int k0 = min((int)floor(Z), ncz - 1);
+        const double wz = Z - k0;
+        const int k1 = min(k0 + 1, ncz - 1);
+        if (k0 != kc0 || k1 != kc1) {
+            c0 = (1.0 - wy) * line(k0, j0) + wy * line(k0, j1);
+            c1 = (1.0 - wy) * line(k1, j0) + wy * line(k1, j1);
+            kc0 = k0;
+            kc1 = k1;
+        }
+        p[ws_at(g, i + 1, j + 1, k + 1)] += s * ((1.0 - wz) * c0 + wz * c1);
+    }
 }
 
 }  // namespace
@@ -214,7 +261,8 @@ bool ws_factor_ok(int nx, int ny, int nz, int f)
 size_t ws_scratch_doubles(int nx, int ny, int nz, int f)
 {
     const size_t ncx = (size_t)(nx / f), ncy = (size_t)(ny / f);
-    return 2 * (size_t)nz * ny * ncx + 2 * (size_t)nz * ncy * ncx;
+    // residual, x-pass sums, y-pass sums, x weight table
+    return (size_t)nx * ny * nz + 2 * (size_t)nz * ny * ncx + 2 * (size_t)nz * ncy * ncx + 2 * (size_t)nx;
 }
 
 gbsw_status launch_ws_restrict(const float *b, const double *p, const WsGrid &g, double dx, int f, double *scratch,
@@ -222,11 +270,14 @@ gbsw_status launch_ws_restrict(const float *b, const double *p, const WsGrid &g,
 {
     if (!ws_factor_ok(g.nx, g.ny, g.nz, f)) return GBSW_ERR_ARG;
     const int ncx = g.nx / f, ncy = g.ny / f;
+    const long long n0 = (long long)g.nx * g.ny * g.nz;
     const long long n1 = (long long)g.nz * g.ny * ncx, n2 = (long long)g.nz * ncy * ncx;
     const long long nc = (long long)(g.nz / f) * ncy * ncx;
-    double *ar = scratch, *ap = ar + n1, *br = ap + n1, *bp = br + n2;
+    double *res = scratch, *ar = res + n0, *ap = ar + n1, *br = ap + n1, *bp = br + n2, *wx = bp + n2;
     auto blocks = [](long long n) { return (unsigned)((n + WS_THREADS - 1) / WS_THREADS); };
-    ws_fw_x_kernel<<<blocks(n1), WS_THREADS, 0, s>>>(b, p, g, dx, f, ar, ap);
+    ws_resid_kernel<<<blocks(n0), WS_THREADS, 0, s>>>(b, p, g, 1.0 / (dx * dx), res);
+    ws_wtab_kernel<<<blocks(2LL * g.nx), WS_THREADS, 0, s>>>(g.nx, ncx, f, 2, wx);
+    ws_fw_x_kernel<<<blocks(n1), WS_THREADS, 0, s>>>(res, p, g, f, wx, ar, ap);
     ws_fw_y_kernel<<<blocks(n2), WS_THREADS, 0, s>>>(ar, ap, g.nz, g.ny, ncx, f, br, bp);
     ws_fw_z_kernel<<<blocks(nc), WS_THREADS, 0, s>>>(br, bp, g.nz, ncy, ncx, f, rc, pc);
     GBSW_LAUNCH_CHECK();
@@ -245,7 +296,7 @@ gbsw_status launch_ws_prolong(const float *out, const WsGrid &g, int f, const do
                               cudaStream_t s)
 {
     if (!ws_factor_ok(g.nx, g.ny, g.nz, f)) return GBSW_ERR_ARG;
-    const long long n = (long long)g.nx * g.ny * g.nz;
+    const long long n = (long long)g.nx * g.ny * ((g.nz + WS_KCH - 1) / WS_KCH);
     ws_prolong_kernel<<<(unsigned)((n + WS_THREADS - 1) / WS_THREADS), WS_THREADS, 0, s>>>(out, g, f, scale, p);
     GBSW_LAUNCH_CHECK();
     return GBSW_OK;
