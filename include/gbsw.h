@@ -351,7 +351,14 @@ gbsw_status les_create(const gbsw_les_params *params, const uint8_t *solid, void
  */
 gbsw_status les_step(gbsw_les *les, int nsteps, gbsw_les_stats *stats);
 
-/* Copy one field to / from a host buffer (layout above).  Synchronous. */
+/* Copy one field to / from a host buffer (layout above).  Synchronous.
+ * A pinned host buffer is read or written by the copy engine directly; a
+ * pageable one goes through a pinned staging buffer of the context
+ * (allocated on first use with the size of one padded field, freed by
+ * les_destroy), because a pitched copy to pageable memory is two orders of
+ * magnitude slower (61 ms against 0.4 ms for the 256x256x128 FP64
+ * pressure on a GB300).  GBSW_ERR_OOM if the staging buffer cannot be
+ * allocated. */
 gbsw_status les_get_field(gbsw_les *les, int field, void *host);
 gbsw_status les_set_field(gbsw_les *les, int field, const void *host);
 

@@ -439,6 +439,8 @@ struct gbsw_les {
     double *ws_scratch;    // restriction passes of the warm start
     size_t ws_scratch_n;
     size_t n;              // elements per padded field
+    void *host_stage;      // pinned staging buffer of field copies to / from pageable memory
+    size_t host_stage_bytes;
 };
 
 namespace {
@@ -508,6 +510,34 @@ gbsw_status les_predictor(gbsw_les *s)
     les_rhs_kernel<<<g1, b1, 0, s->stream>>>(q, s->U[bset], s->V[bset], s->W[bset], s->b);
     GBSW_LAUNCH_CHECK();
     s->cur = bset;
+    return GBSW_OK;
+}
+
+// True for host memory the copy engines reach directly (pinned or mapped).
+bool host_is_pinned(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();  // plain pageable memory on some drivers: not an error of this context
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
+gbsw_status ensure_host_stage(gbsw_les *s, size_t bytes)
+{
+    if (bytes <= s->host_stage_bytes) return GBSW_OK;
+    if (s->host_stage) cudaFreeHost(s->host_stage);
+    s->host_stage = nullptr;
+    s->host_stage_bytes = 0;
+    // the largest field (the FP64 pressure), so that one allocation serves every field
+    const size_t want = std::max(bytes, (size_t)(s->q.d.nx + 2) * (s->q.d.ny + 2) * (s->q.d.nz + 2) * sizeof(double));
+    if (cudaHostAlloc(&s->host_stage, want, cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        s->host_stage = nullptr;
+        return GBSW_ERR_OOM;
+    }
+    s->host_stage_bytes = want;
     return GBSW_OK;
 }
 
@@ -694,17 +724,19 @@ gbsw_status les_get_field(gbsw_les *s, int field, void *host)
 {
     if (!s || !host) return GBSW_ERR_ARG;
     const PDims &d = s->q.d;
-    const size_t rows = (size_t)(d.ny + 2) * (size_t)(d.nz + 2);
-    if (field == GBSW_LES_P) {
-        GBSW_CUDA_TRY(cudaMemcpy2DAsync(host, (d.nx + 2) * sizeof(double), s->solver.p_hi, d.pitch * sizeof(double),
-                                        (d.nx + 2) * sizeof(double), rows, cudaMemcpyDeviceToHost, s->stream));
-    } else {
-        float *src = field_f32(s, field);
-        if (!src) return GBSW_ERR_ARG;
-        GBSW_CUDA_TRY(cudaMemcpy2DAsync(host, (d.nx + 2) * sizeof(float), src, d.pitch * sizeof(float),
-                                        (d.nx + 2) * sizeof(float), rows, cudaMemcpyDeviceToHost, s->stream));
+    const size_t elt = field == GBSW_LES_P ? sizeof(double) : sizeof(float);
+    const void *src = field == GBSW_LES_P ? (const void *)s->solver.p_hi : (const void *)field_f32(s, field);
+    if (!src) return GBSW_ERR_ARG;
+    const size_t rows = (size_t)(d.ny + 2) * (size_t)(d.nz + 2), width = (size_t)(d.nx + 2) * elt;
+    const bool direct = host_is_pinned(host);
+    if (!direct) {
+        const gbsw_status st = ensure_host_stage(s, width * rows);
+        if (st != GBSW_OK) return st;
     }
+    GBSW_CUDA_TRY(cudaMemcpy2DAsync(direct ? host : s->host_stage, width, src, d.pitch * elt, width, rows,
+                                    cudaMemcpyDeviceToHost, s->stream));
     GBSW_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    if (!direct) memcpy(host, s->host_stage, width * rows);
     return GBSW_OK;
 }
 
@@ -712,16 +744,18 @@ gbsw_status les_set_field(gbsw_les *s, int field, const void *host)
 {
     if (!s || !host) return GBSW_ERR_ARG;
     const PDims &d = s->q.d;
-    const size_t rows = (size_t)(d.ny + 2) * (size_t)(d.nz + 2);
-    if (field == GBSW_LES_P) {
-        GBSW_CUDA_TRY(cudaMemcpy2DAsync(s->solver.p_hi, d.pitch * sizeof(double), host, (d.nx + 2) * sizeof(double),
-                                        (d.nx + 2) * sizeof(double), rows, cudaMemcpyHostToDevice, s->stream));
-    } else {
-        float *dst = field_f32(s, field);
-        if (!dst) return GBSW_ERR_ARG;
-        GBSW_CUDA_TRY(cudaMemcpy2DAsync(dst, d.pitch * sizeof(float), host, (d.nx + 2) * sizeof(float),
-                                        (d.nx + 2) * sizeof(float), rows, cudaMemcpyHostToDevice, s->stream));
+    const size_t elt = field == GBSW_LES_P ? sizeof(double) : sizeof(float);
+    void *dst = field == GBSW_LES_P ? (void *)s->solver.p_hi : (void *)field_f32(s, field);
+    if (!dst) return GBSW_ERR_ARG;
+    const size_t rows = (size_t)(d.ny + 2) * (size_t)(d.nz + 2), width = (size_t)(d.nx + 2) * elt;
+    const bool direct = host_is_pinned(host);
+    if (!direct) {
+        const gbsw_status st = ensure_host_stage(s, width * rows);
+        if (st != GBSW_OK) return st;
+        memcpy(s->host_stage, host, width * rows);
     }
+    GBSW_CUDA_TRY(cudaMemcpy2DAsync(dst, d.pitch * elt, direct ? host : s->host_stage, width, width, rows,
+                                    cudaMemcpyHostToDevice, s->stream));
     GBSW_CUDA_TRY(cudaStreamSynchronize(s->stream));
     return GBSW_OK;
 }
@@ -822,6 +856,7 @@ void les_destroy(gbsw_les *s)
     cudaFree(s->face);
     cudaFree(s->ctl_log);
     cudaFree(s->ws_scratch);
+    if (s->host_stage) cudaFreeHost(s->host_stage);
     s->solver.release();
     delete s;
 }

@@ -12,6 +12,16 @@ from ._native_ext import LESParams, LESState, LESStats
 
 FIELDS = dict(u=0, v=1, w=2, p=3, fuo=4, fvo=5, fwo=6, gu=7, gv=8, gw=9, nut=10, b=11)
 
+def _host_empty(shape, dtype) -> np.ndarray:
+    """An uninitialised host array in page-locked memory, which the copy
+    engine reads and writes directly (a pageable array goes through the
+    library's staging buffer), from torch's caching host allocator: the
+    array keeps its block alive, and a freed block serves the next array."""
+    import torch
+    t = torch.empty(shape, dtype=torch.float64 if dtype == np.float64 else torch.float32, pin_memory=True)
+    return t.numpy()
+
+
 DEFAULTS = dict(dx=4.0, dt=0.025, u_ref=5.0, z_ref=10.0, z0=0.1, cs=0.1, nu=1.5e-5, alpha=-100.0, beta=-10.0,
                 omega=1.8, tol=1e-6, max_iter=100000, check_every=10)
 
@@ -43,7 +53,7 @@ class LES:
 
     def get(self, name: str) -> np.ndarray:
         nz, ny, nx = self.shape
-        out = np.empty((nz + 2, ny + 2, nx + 2), dtype=np.float64 if name == "p" else np.float32)
+        out = _host_empty((nz + 2, ny + 2, nx + 2), np.float64 if name == "p" else np.float32)
         N.check(N.lib().les_get_field(self._h, FIELDS[name], out.ctypes.data_as(C.c_void_p)), "les_get_field")
         return out
 
@@ -60,7 +70,7 @@ class LES:
         """Checkpoint: every field the next step depends on (padded layout)
         and the step count."""
         nz, ny, nx = self.shape
-        out = {n: np.empty((nz + 2, ny + 2, nx + 2), dtype=np.float64 if n == "p" else np.float32)
+        out = {n: _host_empty((nz + 2, ny + 2, nx + 2), np.float64 if n == "p" else np.float32)
                for n in self.STATE}
         st = LESState(*[out[n].ctypes.data for n in self.STATE], 0)
         N.check(N.lib().les_get_state(self._h, C.byref(st)), "les_get_state")
