@@ -196,24 +196,37 @@ ws_prepare_kernel(const double *__restrict__ rc, const double *__restrict__ pc, 
 }
 
 // p += s * prolong(out) on the fine cells of column (i, j), planes
-// WS_KCH c .. WS_KCH c + WS_KCH - 1 (one thread).  The x and y
-// interpolation of the two coarse planes k0, k1 (c0, c1) is formed again
-// only when they change along the column; each cell then takes the z
-// interpolation, the same expressions in the same order as a cell-by-cell
-// evaluation.
+// WS_KCH ch .. WS_KCH ch + WS_KCH - 1 (one thread; grid (columns / block,
+// chunks)).  The block forms the chunk's z weights once in shared memory;
+// the x and y interpolation of the two coarse planes k0, k1 (c0, c1) is
+// formed again only when they change along the column; each cell then
+// takes the z interpolation: the same expressions in the same order as a
+// cell-by-cell evaluation.
 constexpr int WS_KCH = 8;
 __global__ void __launch_bounds__(WS_THREADS)
 ws_prolong_kernel(const float *__restrict__ out, WsGrid g, int f, const double *__restrict__ scale,
                   double *__restrict__ p)
 {
-    const int nch = (g.nz + WS_KCH - 1) / WS_KCH;
-    const long long n = (long long)g.nx * g.ny * nch;
+    __shared__ double zw[WS_KCH];
+    __shared__ int zk0[WS_KCH], zk1[WS_KCH];
+    const int ch = blockIdx.y;
+    const int ncx = g.nx / f, ncy = g.ny / f, ncz = g.nz / f;
+    const double inv = 1.0 / f;
+    if (threadIdx.x < WS_KCH) {
+        // z: held at the ground and the lid
+        const int k = ch * WS_KCH + threadIdx.x;
+        const double Z = fmin(fmax((k + 0.5) * inv - 0.5, 0.0), ncz - 1.0);
+        const int k0 = min((int)floor(Z), ncz - 1);
+        zw[threadIdx.x] = Z - k0;
+        zk0[threadIdx.x] = k0;
+        zk1[threadIdx.x] = min(k0 + 1, ncz - 1);
+    }
+    __syncthreads();
+    const long long n = (long long)g.nx * g.ny;
     const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= n) return;
     const double s = *scale;
-    const int i = (int)(v % g.nx), j = (int)((v / g.nx) % g.ny), ch = (int)(v / ((long long)g.nx * g.ny));
-    const int ncx = g.nx / f, ncy = g.ny / f, ncz = g.nz / f;
-    const double inv = 1.0 / f;
+    const int i = (int)(v % g.nx), j = (int)(v / g.nx);
     // x: held at the inflow, antisymmetric ghost past the outflow
     const double X = fmax((i + 0.5) * inv - 0.5, 0.0);
     const int i0 = min((int)floor(X), ncx - 1);
@@ -235,11 +248,9 @@ ws_prolong_kernel(const float *__restrict__ out, WsGrid g, int f, const double *
     double c0 = 0.0, c1 = 0.0;
     const int kend = min((ch + 1) * WS_KCH, g.nz);
     for (int k = ch * WS_KCH; k < kend; ++k) {
-        // z: held at the ground and the lid
-        const double Z = fmin(fmax((k + 0.5) * inv - 0.5, 0.0), ncz - 1.0);
-        const int k0 = min((int)floor(Z), ncz - 1);
-        const double wz = Z - k0;
-        const int k1 = min(k0 + 1, ncz - 1);
+        const int e = k - ch * WS_KCH;
+        const int k0 = zk0[e], k1 = zk1[e];
+        const double wz = zw[e];
         if (k0 != kc0 || k1 != kc1) {
             c0 = (1.0 - wy) * line(k0, j0) + wy * line(k0, j1);
             c1 = (1.0 - wy) * line(k1, j0) + wy * line(k1, j1);
@@ -296,8 +307,9 @@ gbsw_status launch_ws_prolong(const float *out, const WsGrid &g, int f, const do
                               cudaStream_t s)
 {
     if (!ws_factor_ok(g.nx, g.ny, g.nz, f)) return GBSW_ERR_ARG;
-    const long long n = (long long)g.nx * g.ny * ((g.nz + WS_KCH - 1) / WS_KCH);
-    ws_prolong_kernel<<<(unsigned)((n + WS_THREADS - 1) / WS_THREADS), WS_THREADS, 0, s>>>(out, g, f, scale, p);
+    const long long n = (long long)g.nx * g.ny;
+    const dim3 grid((unsigned)((n + WS_THREADS - 1) / WS_THREADS), (unsigned)((g.nz + WS_KCH - 1) / WS_KCH));
+    ws_prolong_kernel<<<grid, WS_THREADS, 0, s>>>(out, g, f, scale, p);
     GBSW_LAUNCH_CHECK();
     return GBSW_OK;
 }

@@ -234,6 +234,35 @@ def test_checkpoint_restart_is_bit_identical(G):
             assert np.array_equal(c.get(n)[INT], ref[n][INT]), n
 
 
+def test_field_copies_through_pinned_and_pageable_buffers_agree(G):
+    """les_get_field / les_set_field copy a page-locked host buffer directly
+    and a pageable one through the context's staging buffer: both move the
+    same bytes, in both directions."""
+    import ctypes as C
+
+    import torch
+
+    from paper_1711_04471_gb300 import _native as N
+    nx, ny, nz, solid = small_case(32, 16, 12, seed=3)
+    with G.LES(nx, ny, nz, solid) as g:
+        g.step(2)
+        for name in ("p", "u", "gu"):
+            dt = np.float64 if name == "p" else np.float32
+            pinned = g.get(name)                       # the binding's page-locked array
+            assert torch.from_numpy(pinned).is_pinned()
+            pageable = np.empty(pinned.shape, dt)
+            N.check(N.lib().les_get_field(g._h, G.FIELDS[name], pageable.ctypes.data_as(C.c_void_p)), "get")
+            assert np.array_equal(pinned, pageable), name
+            new = pageable * 1.5 + 0.25                # written from pageable memory, read back pinned
+            N.check(N.lib().les_set_field(g._h, G.FIELDS[name], new.ctypes.data_as(C.c_void_p)), "set")
+            assert np.array_equal(g.get(name), new), name
+            src = torch.from_numpy(pageable).pin_memory()   # written from pinned memory, read back pageable
+            N.check(N.lib().les_set_field(g._h, G.FIELDS[name], C.c_void_p(src.data_ptr())), "set")
+            back = np.empty(pinned.shape, dt)
+            N.check(N.lib().les_get_field(g._h, G.FIELDS[name], back.ctypes.data_as(C.c_void_p)), "get")
+            assert np.array_equal(back, pageable), name
+
+
 def test_whole_state_checkpoint_restart_is_bit_identical(G):
     """les_get_state / les_set_state: a context restored from a checkpoint
     takes bitwise the steps the original takes."""
