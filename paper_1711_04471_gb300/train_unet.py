@@ -21,19 +21,17 @@ coarse tensors by augment), and any linear combination of pairs is a pair
 Everything runs through the C ABI (les_*, warm_start_*, unet_*); the samples
 stay in device memory.
 
-The committed weights come from 28 runs of base seed 5000 (k = 0..27; the
+The committed weights come from 56 runs of base seed 5000 (k = 0..55; the
 last one held out for validation), each 200 solved steps after one solved
-start-up step: 5,400 training pairs, 172,800 with the shifted and mirrored
-copies.  The runs used the previously committed weights (trained on 13
-shorter runs) as their warm start, which only shortens the solves: every
-target is the solver's pressure at the 1e-6 residual.  Generated in four
-calls (the pairs of 8 runs are about 37 MB) and trained on together:
+start-up step: 11,000 training pairs, 352,000 with the shifted and
+mirrored copies.  The runs used the previously committed weights (trained
+the same way on 28 runs) as their warm start, which only shortens the
+solves: every target is the solver's pressure at the 1e-6 residual.  One
+call generates the pairs and trains (about 24 minutes of generation and 4
+of training on one GB300; the pairs stay in device memory):
 
-    python -m paper_1711_04471_gb300.train_unet --seeds 4 --first-seed 0 --base-seed 5000 --steps 200 --start 1 \
-        --iters 0 --out /tmp/x.npy --save-data gen_5000_0.npz --gen-weights previous_weights.npy
-    (likewise --seeds 8 --first-seed 4, 12 and 20 into gen_5000_4/12/20.npz)
-    python -m paper_1711_04471_gb300.train_unet --data gen_5000_0.npz gen_5000_4.npz gen_5000_12.npz gen_5000_20.npz \
-        --iters 100000 --out weights.npy
+    python -m paper_1711_04471_gb300.train_unet --seeds 56 --base-seed 5000 --steps 200 --start 1 \
+        --gen-weights previous_weights.npy --iters 150000 --out weights.npy
 """
 from __future__ import annotations
 
