@@ -391,12 +391,14 @@ gbsw_status les_set_solver(gbsw_les *les, double omega, double tol, int max_iter
  * falls geometrically, so after each check the next one is placed at the
  * iteration where the rate measured between the last two checks reaches
  * the tolerance (with a 3 % + 1 iteration margin), never more than
- * check_every iterations on; the sweeps of the loop body past that point
- * return at once.  The iterates and the FP64 stopping test (Sec. 6.3.1,
- * press) are unchanged: a step stops at the first check whose residual is
- * within tol, as before, only with fewer wasted iterations between the
- * tolerance and the check.  Off: a check every check_every iterations.
- * The standalone poisson_solve always checks every check_every iterations. */
+ * check_every iterations on.  The solve loop runs chunks of iterations (the
+ * largest divisor of check_every up to 50, or 50 when that divisor is
+ * below 12) and takes the check at the first chunk boundary at or past
+ * that point.  The iterates and the FP64 stopping test (Sec. 6.3.1, press)
+ * are unchanged: a step stops at the first check whose residual is within
+ * tol, as before, only with fewer wasted iterations between the tolerance
+ * and the check.  Off: a check every check_every iterations.  The
+ * standalone poisson_solve always checks every check_every iterations. */
 gbsw_status les_set_check_prediction(gbsw_les *les, int on);
 
 /* Paper mode (Sec. 6.3.2 runs UFLES with the number of SOR iterations set

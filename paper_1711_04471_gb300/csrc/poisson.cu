@@ -525,7 +525,8 @@ gbsw_status PoissonSolver::build_graph()
 
 // The solve graph with predicted checks: prelude (e = 0, first residual,
 // test), then a while node whose body is a chunk of c iterations (c the
-// largest divisor of m up to SOR_CHUNK_MAX), poisson_due_kernel, an if
+// largest divisor of m up to SOR_CHUNK_MAX, or SOR_CHUNK_MAX when that
+// divisor is small), poisson_due_kernel, an if
 // node holding the check (fold, FP64 residual, test with prediction) and
 // poisson_continue_kernel.  Every chunk starts from the correction as the
 // last chunk or check left it; after a check it is 0, where the general
@@ -543,6 +544,11 @@ gbsw_status PoissonSolver::build_graph_predicted()
             c = x;
             break;
         }
+    // An interval with no divisor near SOR_CHUNK_MAX (a prime above it, say)
+    // would give chunks of a few iterations, each paying two control
+    // kernels: take full chunks, and the check then comes at the first
+    // chunk boundary at or past the interval.
+    if (c < SOR_CHUNK_MAX / 4 && m > SOR_CHUNK_MAX) c = SOR_CHUNK_MAX;
     const size_t nc = (size_t)d.cplane * (size_t)(d.nz + 2);
     const float om = (float)omega, h2 = (float)(d.dx * d.dx);
     const int nxh = (d.nx + 1) / 2;
