@@ -57,6 +57,7 @@ __device__ __forceinline__ bool index_ok(long long i, long long n, unsigned *cou
 unsigned long long take_bounds_sw();
 unsigned long long take_bounds_batch();
 unsigned long long take_bounds_poisson();
+unsigned long long take_bounds_les();
 
 // Remember the last CUDA error text for diagnostics.
 void record_cuda_error(cudaError_t e, const char *what, const char *file, int line);

@@ -30,6 +30,21 @@
 #include "unet_ops.cuh"
 #include "warmstart.cuh"
 
+namespace gbsw {
+
+// Out-of-range index count of the bounds-checked debug build.
+static __device__ unsigned g_les_bounds;
+
+unsigned long long take_bounds_les()
+{
+    unsigned h = 0, zero = 0;
+    if (cudaMemcpyFromSymbol(&h, g_les_bounds, sizeof(h)) != cudaSuccess) return 0;
+    cudaMemcpyToSymbol(g_les_bounds, &zero, sizeof(zero));
+    return h;
+}
+
+}  // namespace gbsw
+
 using namespace gbsw;
 
 namespace {
@@ -49,6 +64,10 @@ __device__ __forceinline__ long long L(const PDims &d, int i, int j, int k)
     return (long long)k * d.plane + (long long)j * d.pitch + i;
 }
 
+// Index test of the bounds-checked build: c inside a padded field
+// ((nz+2) planes); always true in the product build.
+#define LES_OK(d, c) GBSW_INBOUNDS((c), (long long)(d).plane * ((d).nz + 2), &g_les_bounds)
+
 // velnw: projection with the previous pressure, interior faces only.
 __global__ void les_velnw_kernel(LDev q, const double *__restrict__ p, float *__restrict__ u, float *__restrict__ v,
                                  float *__restrict__ w)
@@ -57,10 +76,11 @@ __global__ void les_velnw_kernel(LDev q, const double *__restrict__ p, float *__
     const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
     const int j = blockIdx.y + 1, k = blockIdx.z + 1;
     if (i > d.nx) return;
-    const long long c = L(d, i, j, k);
+    const long long c = L(d, i, j, k), cn = L(d, i, (j < d.ny) ? j + 1 : 1, k);
+    if (!LES_OK(d, c) || !LES_OK(d, c + 1) || !LES_OK(d, cn) || !LES_OK(d, c + d.plane)) return;
     const double pc = p[c];
     const double pe = (i < d.nx) ? p[c + 1] : -pc;
-    const double pn = p[L(d, i, (j < d.ny) ? j + 1 : 1, k)];
+    const double pn = p[cn];
     u[c] -= q.c_grad * (float)(pe - pc);
     v[c] -= q.c_grad * (float)(pn - pc);
     if (k < d.nz) w[c] -= q.c_grad * (float)(p[c + d.plane] - pc);
@@ -158,11 +178,11 @@ __device__ __forceinline__ LtVel lt_fetch_plane(const LDev &q, const LtMap &m, i
     const int kc = kk <= 0 ? 1 : (kk >= d.nz + 1 ? d.nz : kk);
     const bool ground = kk == 0, wzero = kk == 0 || kk >= d.nz;
     const long long base = (long long)kc * d.plane;
-    const float uin_k = ok ? uin[kc] : 0.0f;
+    const float uin_k = ok && GBSW_INBOUNDS(kc, d.nz + 2, &g_les_bounds) ? uin[kc] : 0.0f;
 #pragma unroll
     for (int c = 0; c < LT_LPT; ++c) {
         float a = 0.0f, b = 0.0f, cw = 0.0f;
-        if (ok && m.src[c] >= 0) {
+        if (ok && m.src[c] >= 0 && LES_OK(d, base + m.src[c])) {
             const long long cc = base + m.src[c];
             const bool in = (m.inflow >> c) & 1u;
             const float uu = in ? uin_k : u[cc];
@@ -243,7 +263,7 @@ __device__ __forceinline__ void lt_nut_plane(const LDev &q, LesTileSmem &sm, con
         const float ss = 2.0f * (s11 * s11 + s22 * s22 + s33 * s33) + (a12 + a13 + a23);
         const float nt = q.l2 * sqrtf(ss);
         ne[threadIdx.x + c * LT_THREADS] = nt;
-        if (write && m.out[c] >= 0) nut_out[base + m.out[c]] = nt;
+        if (write && m.out[c] >= 0 && LES_OK(d, base + m.out[c])) nut_out[base + m.out[c]] = nt;
     }
 }
 
@@ -387,7 +407,7 @@ les_predict_tile_kernel(LDev q, int first, const float *__restrict__ u, const fl
     for (int k = k0 + 1; k <= k1; ++k) {
         uint8_t fl = 0;
         float fuo_c = 0.0f, fvo_c = 0.0f, fwo_c = 0.0f;
-        if (own) {  // the predictor's own global reads, issued first
+        if (own && LES_OK(d, L(d, i, j, k)) && LES_OK(d, L(d, i, j, k) - 1)) {  // the predictor's own global reads, issued first
             const long long c = L(d, i, j, k);
             fl = face[c];
             fuo_c = fuo[c];
@@ -399,7 +419,7 @@ les_predict_tile_kernel(LDev q, int first, const float *__restrict__ u, const fl
         if (k + 1 <= k1) ahead = lt_fetch_plane(q, m, k + 3, u, v, w, uin);  // consumed by the next plane step
         lt_nut_plane(q, sm, m, k + 1, k + 1 <= k1, nut);
         __syncthreads();
-        if (own)
+        if (own && LES_OK(d, L(d, i, j, k)) && LES_OK(d, L(d, i, j, k) - 1))
             lt_predict_cell(q, sm, k, i, j, o, on, first != 0, fl, fuo_c, fvo_c, fwo_c, us, vs, ws, fuo, fvo, fwo, gu,
                             gv, gw);
     }
@@ -413,8 +433,9 @@ __global__ void les_rhs_kernel(LDev q, const float *__restrict__ u, const float 
     const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
     const int j = blockIdx.y + 1, k = blockIdx.z + 1;
     if (i > d.nx) return;
-    const long long c = L(d, i, j, k);
-    const float vs = v[L(d, i, (j > 1) ? j - 1 : d.ny, k)];
+    const long long c = L(d, i, j, k), cs = L(d, i, (j > 1) ? j - 1 : d.ny, k);
+    if (!LES_OK(d, c) || !LES_OK(d, c - 1) || !LES_OK(d, cs) || !LES_OK(d, c - d.plane)) return;
+    const float vs = v[cs];
     const float wb = k > 1 ? w[c - d.plane] : 0.0f;  // the ground face is closed
     b[c] = q.rdxdt * ((u[c] - u[c - 1]) + (v[c] - vs) + (w[c] - wb));
 }

@@ -67,7 +67,8 @@ extern "C" gbsw_status gbsw_debug_bounds(long long *violations)
         return GBSW_OK;
     }
     GBSW_CUDA_TRY(cudaDeviceSynchronize());
-    const unsigned long long n = gbsw::take_bounds_sw() + gbsw::take_bounds_batch() + gbsw::take_bounds_poisson();
+    const unsigned long long n = gbsw::take_bounds_sw() + gbsw::take_bounds_batch() + gbsw::take_bounds_poisson() +
+                                 gbsw::take_bounds_les();
     *violations = (long long)n;
     return n ? GBSW_ERR_DEVICE_BOUNDS : GBSW_OK;
 }

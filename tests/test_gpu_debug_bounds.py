@@ -3,9 +3,11 @@
 gbsw_selftest_bounds feeds the index test an index one past the end of a
 buffer (no access is made): the violation is counted and reported.  Then the
 2DSW kernels (streaming with several segment heights, the tile kernel, the
-ensemble kernel) and the SOR solve (warp-per-row and flat thread mappings)
-run in the debug library in a child process: no index leaves its buffer,
-and every result equals the product build's bit for bit."""
+ensemble kernel), the SOR solve (warp-per-row and flat thread mappings) and
+the UFLES predictor kernels (velnw, the fused predictor, the right-hand
+side; whole and ragged tiles) run in the debug library in a child process:
+no index leaves its buffer, and every result equals the product build's
+bit for bit."""
 import json
 import os
 import subprocess
@@ -46,6 +48,14 @@ for nx, ny, nz in [(256, 64, 9), (150, 40, 7)]:
     p = torch.zeros_like(bb)
     poisson_solve(p, bb, 4.0, tol=-1.0, max_iter=60, check_every=50)
     out[f"sor_{nx}"] = p.cpu().numpy()
+from paper_1711_04471_gb300.les import LES
+for nx, ny, nz in [(40, 32, 20), (37, 30, 11)]:   # whole and ragged tiles, chunks of planes
+    solid = inputs.les_buildings(nx, ny, nz, dx=4.0, seed=5, cover=0.2, margin_cells=4)
+    with LES(nx, ny, nz, solid) as g:
+        g.set_fixed_iterations(20)
+        g.step(3, stats=False)
+        for name in ("u", "v", "w", "p", "nut", "b"):
+            out[f"les_{nx}_{name}"] = g.get(name)[1:-1, 1:-1, 1:-1].copy()
 v = C.c_longlong()
 st = N.lib().gbsw_debug_bounds(C.byref(v))
 np.savez(OUT, **out)
