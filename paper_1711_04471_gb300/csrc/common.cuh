@@ -58,6 +58,7 @@ unsigned long long take_bounds_sw();
 unsigned long long take_bounds_batch();
 unsigned long long take_bounds_poisson();
 unsigned long long take_bounds_les();
+unsigned long long take_bounds_ws();
 
 // Remember the last CUDA error text for diagnostics.
 void record_cuda_error(cudaError_t e, const char *what, const char *file, int line);

@@ -68,7 +68,7 @@ extern "C" gbsw_status gbsw_debug_bounds(long long *violations)
     }
     GBSW_CUDA_TRY(cudaDeviceSynchronize());
     const unsigned long long n = gbsw::take_bounds_sw() + gbsw::take_bounds_batch() + gbsw::take_bounds_poisson() +
-                                 gbsw::take_bounds_les();
+                                 gbsw::take_bounds_les() + gbsw::take_bounds_ws();
     *violations = (long long)n;
     return n ? GBSW_ERR_DEVICE_BOUNDS : GBSW_OK;
 }

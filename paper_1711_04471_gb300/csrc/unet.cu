@@ -351,7 +351,7 @@ gbsw_status unet_warm_start(gbsw_unet *u, const float *b, double *p, const PadDi
     if (!ws_factor_ok(pd.nx, pd.ny, pd.nz, f)) return GBSW_ERR_ARG;
     Acts *a = nullptr;
     TRY(get_acts(u, 1, pd.nz / f, pd.ny / f, pd.nx / f, false, &a));
-    const WsGrid g{pd.nx, pd.ny, pd.nz, pd.pitch, pd.plane, pd.plane + pd.pitch + 1};
+    const WsGrid g{pd.nx, pd.ny, pd.nz, pd.pitch, pd.plane, pd.plane + pd.pitch + 1, pd.plane * (pd.nz + 2)};
     const long long nc = a->nvox;
     TRY(launch_ws_restrict(b, p, g, dx, f, scratch, a->ws, a->ws + nc, s));
     TRY(launch_ws_prepare(a->ws, a->ws + nc, nc, (f * dx) * (f * dx), a->xin, a->ws + 2 * nc, s));

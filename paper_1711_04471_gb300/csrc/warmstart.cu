@@ -21,6 +21,21 @@
 
 namespace gbsw {
 
+// Out-of-range index count of the bounds-checked debug build.
+static __device__ unsigned g_ws_bounds;
+
+unsigned long long take_bounds_ws()
+{
+    unsigned h = 0, zero = 0;
+    if (cudaMemcpyFromSymbol(&h, g_ws_bounds, sizeof(h)) != cudaSuccess) return 0;
+    cudaMemcpyToSymbol(g_ws_bounds, &zero, sizeof(zero));
+    return h;
+}
+
+// Index test of the bounds-checked build on a field of the grid; always
+// true in the product build.
+#define WS_OK(g, c) GBSW_INBOUNDS((c), (g).extent, &g_ws_bounds)
+
 namespace {
 
 constexpr int WS_THREADS = 256;
@@ -68,7 +83,7 @@ ws_resid_kernel(const float *__restrict__ b, const double *__restrict__ p, WsGri
     const int k = (int)(q / ((long long)g.nx * g.ny)) + 1;
     const int jm = j == 1 ? g.ny : j - 1, jp = j == g.ny ? 1 : j + 1;
     auto P = [&](int ii, int jj, int kk) -> double {
-        if (ii < 1 || ii > g.nx || kk < 1 || kk > g.nz) return 0.0;
+        if (ii < 1 || ii > g.nx || kk < 1 || kk > g.nz || !WS_OK(g, ws_at(g, ii, jj, kk))) return 0.0;
         return p[ws_at(g, ii, jj, kk)];
     };
     const int dci = 6 - (i == 1) - (k == 1) - (k == g.nz) + (i == g.nx);
@@ -76,7 +91,8 @@ ws_resid_kernel(const float *__restrict__ b, const double *__restrict__ p, WsGri
     const double pv = P(i, j, k);
     const double nb = (P(i - 1, j, k) + P(i + 1, j, k)) + (P(i, jm, k) + P(i, jp, k)) +
                       (P(i, j, k - 1) + P(i, j, k + 1));
-    r[q] = (double)b[ws_at(g, i, j, k)] - (nb - diag * pv) * r2;
+    const double bc = WS_OK(g, ws_at(g, i, j, k)) ? (double)b[ws_at(g, i, j, k)] : 0.0;
+    r[q] = bc - (nb - diag * pv) * r2;
 }
 
 // Table of the full-weighting weights along one axis of n fine cells and
@@ -113,7 +129,7 @@ ws_fw_x_kernel(const double *__restrict__ r, const double *__restrict__ p, WsGri
         const double w = wtab[I * 2 * f + (i0 - base)];
         if (w == 0.0) continue;
         sr += w * r[row + i0];
-        sp += w * p[ws_at(g, i0 + 1, j, k)];
+        sp += w * (WS_OK(g, ws_at(g, i0 + 1, j, k)) ? p[ws_at(g, i0 + 1, j, k)] : 0.0);
     }
     ar[q] = sr;
     ap[q] = sp;
@@ -257,7 +273,7 @@ ws_prolong_kernel(const float *__restrict__ out, WsGrid g, int f, const double *
             kc0 = k0;
             kc1 = k1;
         }
-        p[ws_at(g, i + 1, j + 1, k + 1)] += s * ((1.0 - wz) * c0 + wz * c1);
+        if (WS_OK(g, ws_at(g, i + 1, j + 1, k + 1))) p[ws_at(g, i + 1, j + 1, k + 1)] += s * ((1.0 - wz) * c0 + wz * c1);
     }
 }
 
@@ -329,6 +345,7 @@ WsGrid dense_grid(int nx, int ny, int nz)
     g.sy = nx;
     g.sz = (long long)nx * ny;
     g.off = 0;
+    g.extent = (long long)nx * ny * nz;
     return g;
 }
 

@@ -11,6 +11,7 @@ namespace gbsw {
 struct WsGrid {
     int nx, ny, nz;
     long long sy, sz, off;
+    long long extent;  // elements of each field (the bounds-checked build tests indices against it)
 };
 
 // f a power of two (<= 64) dividing nx, ny and nz.

@@ -5,7 +5,8 @@ buffer (no access is made): the violation is counted and reported.  Then the
 2DSW kernels (streaming with several segment heights, the tile kernel, the
 ensemble kernel), the SOR solve (warp-per-row and flat thread mappings) and
 the UFLES predictor kernels (velnw, the fused predictor, the right-hand
-side; whole and ragged tiles) run in the debug library in a child process:
+side; whole and ragged tiles) and the learned warm start's grid transfers
+run in the debug library in a child process:
 no index leaves its buffer, and every result equals the product build's
 bit for bit."""
 import json
@@ -56,6 +57,13 @@ for nx, ny, nz in [(40, 32, 20), (37, 30, 11)]:   # whole and ragged tiles, chun
         g.step(3, stats=False)
         for name in ("u", "v", "w", "p", "nut", "b"):
             out[f"les_{nx}_{name}"] = g.get(name)[1:-1, 1:-1, 1:-1].copy()
+from paper_1711_04471_gb300.unet import UNet
+solid = inputs.les_buildings(64, 64, 32, dx=4.0, seed=6, cover=0.2, margin_cells=4)
+with UNet(seed=0) as net, LES(64, 64, 32, solid) as g:   # the learned warm start's grid transfers
+    g.set_warm_start(net)
+    g.set_fixed_iterations(20)
+    g.step(2, stats=False)
+    out["les_ws_p"] = g.get("p")[1:-1, 1:-1, 1:-1].copy()
 v = C.c_longlong()
 st = N.lib().gbsw_debug_bounds(C.byref(v))
 np.savez(OUT, **out)
