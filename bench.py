@@ -395,9 +395,9 @@ def _timed_region(fn, world):
 
 
 def run_ensemble(args, rank, world, local):
-    """512 2DSW instances (sides log-uniform in [64, 1024]), 100 time steps per
-    bench step: one persistent cooperative kernel per call (CUDA graph) vs one
-    launch per instance and fused level."""
+    """512 2DSW instances (sides log-uniform in [64, 1024]), STEPS_PER_BENCH_STEP
+    time steps per bench step: one persistent cooperative kernel per call
+    (CUDA graph) vs one launch per instance and fused level."""
     import torch
 
     import paper_1711_04471_gb300 as P
@@ -410,7 +410,7 @@ def run_ensemble(args, rank, world, local):
     cells = int(sum(int(n) * int(n) for n in sizes))
     stream = torch.cuda.current_stream()
     b = SWBatch(members, stream=stream)
-    T, rows = b.autotune(trial_steps=12, cache_path=os.environ.get("GBSW_TUNE_CACHE"))
+    T, rows = b.autotune(trial_steps=60, cache_path=os.environ.get("GBSW_TUNE_CACHE"))  # ~25 ms per candidate
     per = STEPS_PER_BENCH_STEP
     for _ in range(args.warmup):
         b.step(per)
@@ -439,7 +439,7 @@ def run_ensemble(args, rank, world, local):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_graph / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"2DSW ensemble: {len(sizes)} instances, sides log-uniform 64..1024, "
-                                   f"{cells} cells, 100 time steps + FP64 volumes per step",
+                                   f"{cells} cells, {per} time steps + FP64 volumes per step",
                        "tiling": {"steps_per_level": T, "rows_per_item": rows}},
             "separate_launches": {"value": cells * per * args.steps * world / t_sep, "unit": "cell-updates/s",
                                   "ms_per_step": t_sep / args.steps * 1e3},
@@ -700,8 +700,8 @@ def run_sw_paper(args, rank, world, local):
 
 def run_sw64(args, rank, world, local):
     """The FP64 variant of the 2DSW step (three kernels per step, every
-    operation rounded as written) on the 4096^2 wet/dry grid: 100 time
-    steps plus the FP64 volume per bench step."""
+    operation rounded as written) on the 4096^2 wet/dry grid:
+    STEPS_PER_BENCH_STEP time steps plus the FP64 volume per bench step."""
     import torch
 
     import paper_1711_04471_gb300 as P
@@ -729,7 +729,7 @@ def run_sw64(args, rank, world, local):
                       "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                       "data": "synthetic",
                       "config": {"workload": "2DSW 4096x4096 wet/dry, FP64 end to end (3 kernels per time step), "
-                                             "100 time steps + FP64 volume per step"},
+                                             f"{STEPS_PER_BENCH_STEP} time steps + FP64 volume per step"},
                       "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                                    "traffic": None, "peak_kind": peak_kind, "kernel": "sw64 momentum/continuity/shapiro",
                                    "per_unit": "120 B per cell-update (48 + 40 + 32 B over the three kernels)"},
