@@ -702,6 +702,7 @@ gbsw_status les_step(gbsw_les *s, int nsteps, gbsw_les_stats *stats)
                 }
                 s->ws_scratch_n = need;
             }
+            s->solver.invalidate_stencil_cache();  // the guess changes p_hi before the solve
             st = unet_warm_start(s->net, s->b, s->solver.p_hi, pd, s->p.dx, f, s->ws_scratch, s->stream);
             if (st != GBSW_OK) break;
         }
@@ -768,6 +769,7 @@ gbsw_status les_set_field(gbsw_les *s, int field, const void *host)
     const size_t elt = field == GBSW_LES_P ? sizeof(double) : sizeof(float);
     void *dst = field == GBSW_LES_P ? (void *)s->solver.p_hi : (void *)field_f32(s, field);
     if (!dst) return GBSW_ERR_ARG;
+    if (field == GBSW_LES_P) s->solver.invalidate_stencil_cache();
     const size_t rows = (size_t)(d.ny + 2) * (size_t)(d.nz + 2), width = (size_t)(d.nx + 2) * elt;
     const bool direct = host_is_pinned(host);
     if (!direct) {

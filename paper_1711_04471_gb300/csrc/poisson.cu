@@ -165,10 +165,15 @@ sor_sweep_kernel(PDims d, int colour, float omega, float h2, SorDiag dg, float *
 // d_c = 6 - [i == 1] - [k == 1] - [k == nz] + [i == nx]: five FP64
 // additions and one FMA per cell.  The kernel is bound by the FP64 pipe,
 // so 1/dx^2 comes from the host and d_c from integer selects.
+// Stencil cache (fixed-count solves): with s_out, the stencil part
+// s = sum of neighbours - d_c p of every cell is also stored (padded FP64
+// layout); with s_in and *s_ok != 0 (p_hi unchanged since it was stored)
+// s is read instead of formed, the same value, so r is bitwise the same.
 template <bool WITH_BB>
 __global__ void __launch_bounds__(POI_RED_THREADS)
 poisson_resid_kernel(PDims d, const float *__restrict__ b, const double *__restrict__ p_hi, float *__restrict__ r0,
-                     float *__restrict__ r1, double *__restrict__ partials)
+                     float *__restrict__ r1, double *__restrict__ partials, const double *__restrict__ s_in,
+                     const int *__restrict__ s_ok, double *__restrict__ s_out)
 {
     __shared__ double red[POI_RED_THREADS / 32];
     const double r2 = d.rdx2;
@@ -177,6 +182,7 @@ poisson_resid_kernel(PDims d, const float *__restrict__ b, const double *__restr
     const int jm = (j == 1) ? d.ny : j - 1;
     const int jp = (j == d.ny) ? 1 : j + 1;
     double rr = 0.0, bb = 0.0;
+    const bool cached = s_in != nullptr && *s_ok != 0;
     if (i <= d.nx) {
         // cells outside the grid in x or z read as 0 (ghost values unused)
         auto P = [&](int ii, int jj, int kk) -> double {
@@ -186,14 +192,20 @@ poisson_resid_kernel(PDims d, const float *__restrict__ b, const double *__restr
         for (int kk = 0; kk < POI_RES_PLANES; ++kk) {
             const int k = blockIdx.z * POI_RES_PLANES + kk + 1;
             if (k > d.nz) break;
-            const double pc = p_hi[pidx(d, i, j, k)];
-            const double nb = (P(i - 1, j, k) + P(i + 1, j, k)) + (P(i, jm, k) + P(i, jp, k)) +
-                              (P(i, j, k - 1) + P(i, j, k + 1));
-            // d_c = 6 - [i == 1] - [k == 1] - [k == nz] + [i == nx] in {4, .., 7}
-            // (nx, nz >= 2), picked by integer selects: no FP64 operation
-            const int dci = 6 - (i == 1) - (k == 1) - (k == d.nz) + (i == d.nx);
-            const double dc = dci == 6 ? 6.0 : (dci == 5 ? 5.0 : (dci == 7 ? 7.0 : 4.0));
-            const double s = fma(-dc, pc, nb);
+            double s;
+            if (cached) {
+                s = s_in[pidx(d, i, j, k)];
+            } else {
+                const double pc = p_hi[pidx(d, i, j, k)];
+                const double nb = (P(i - 1, j, k) + P(i + 1, j, k)) + (P(i, jm, k) + P(i, jp, k)) +
+                                  (P(i, j, k - 1) + P(i, j, k + 1));
+                // d_c = 6 - [i == 1] - [k == 1] - [k == nz] + [i == nx] in {4, .., 7}
+                // (nx, nz >= 2), picked by integer selects: no FP64 operation
+                const int dci = 6 - (i == 1) - (k == 1) - (k == d.nz) + (i == d.nx);
+                const double dc = dci == 6 ? 6.0 : (dci == 5 ? 5.0 : (dci == 7 ? 7.0 : 4.0));
+                s = fma(-dc, pc, nb);
+                if (s_out) s_out[pidx(d, i, j, k)] = s;
+            }
             const double bc = (double)b[pidx(d, i, j, k)];
             const double res = fma(-s, r2, bc);
             float *ra = ((i + j + k) & 1) ? r1 : r0;
@@ -421,6 +433,11 @@ void PoissonSolver::release()
     }
     cudaFree(partials);
     cudaFree(ctl);
+    cudaFree(s_cache);
+    cudaFree(s_ok);
+    s_cache = nullptr;
+    s_ok = nullptr;
+    s_valid_ = false;
     p_hi = nullptr;
     partials = nullptr;
     ctl = nullptr;
@@ -475,7 +492,7 @@ gbsw_status PoissonSolver::build_graph()
         // prelude: e = 0, r = b - A p_hi, ||b||^2, first test
         chk(cudaMemsetAsync(e[0], 0, nc * sizeof(float), cs));
         chk(cudaMemsetAsync(e[1], 0, nc * sizeof(float), cs));
-        poisson_resid_kernel<true><<<rgrid, POI_RED_THREADS, 0, cs>>>(d, b, p_hi, r[0], r[1], partials);
+        poisson_resid_kernel<true><<<rgrid, POI_RED_THREADS, 0, cs>>>(d, b, p_hi, r[0], r[1], partials, nullptr, nullptr, nullptr);
         chk(cudaGetLastError());
         poisson_test_kernel<true><<<1, POI_RED_THREADS, 0, cs>>>(partials, rblocks, ctl, tol, max_iter, m, 0,
                                                                   0, handle);
@@ -505,7 +522,7 @@ gbsw_status PoissonSolver::build_graph()
             chk(launch_iterations(d, m, om, h2, e, r, cs));
             poisson_fold_kernel<<<fgrid, fblock, 0, cs>>>(d, 0, p_hi, e[0]);
             poisson_fold_kernel<<<fgrid, fblock, 0, cs>>>(d, 1, p_hi, e[1]);
-            poisson_resid_kernel<false><<<rgrid, POI_RED_THREADS, 0, cs>>>(d, b, p_hi, r[0], r[1], partials);
+            poisson_resid_kernel<false><<<rgrid, POI_RED_THREADS, 0, cs>>>(d, b, p_hi, r[0], r[1], partials, nullptr, nullptr, nullptr);
             poisson_test_kernel<true><<<1, POI_RED_THREADS, 0, cs>>>(partials, rblocks, ctl, tol, max_iter, m,
                                                                     1, 0, handle);
             chk(cudaGetLastError());
@@ -589,7 +606,7 @@ gbsw_status PoissonSolver::build_graph_predicted()
         // prelude: e = 0, r = b - A p_hi, ||b||^2, first test (next = m)
         chk(cudaMemsetAsync(e[0], 0, nc * sizeof(float), cs));
         chk(cudaMemsetAsync(e[1], 0, nc * sizeof(float), cs));
-        poisson_resid_kernel<true><<<rgrid, POI_RED_THREADS, 0, cs>>>(d, b, p_hi, r[0], r[1], partials);
+        poisson_resid_kernel<true><<<rgrid, POI_RED_THREADS, 0, cs>>>(d, b, p_hi, r[0], r[1], partials, nullptr, nullptr, nullptr);
         chk(cudaGetLastError());
         poisson_test_kernel<true><<<1, POI_RED_THREADS, 0, cs>>>(partials, rblocks, ctl, tol, max_iter, m, 0, 1,
                                                                   hloop);
@@ -619,7 +636,7 @@ gbsw_status PoissonSolver::build_graph_predicted()
         if (err == cudaSuccess) {
             poisson_fold_kernel<<<fgrid, fblock, 0, cs>>>(d, 0, p_hi, e[0]);
             poisson_fold_kernel<<<fgrid, fblock, 0, cs>>>(d, 1, p_hi, e[1]);
-            poisson_resid_kernel<false><<<rgrid, POI_RED_THREADS, 0, cs>>>(d, b, p_hi, r[0], r[1], partials);
+            poisson_resid_kernel<false><<<rgrid, POI_RED_THREADS, 0, cs>>>(d, b, p_hi, r[0], r[1], partials, nullptr, nullptr, nullptr);
             poisson_test_kernel<false><<<1, POI_RED_THREADS, 0, cs>>>(partials, rblocks, ctl, tol, max_iter, m, 1,
                                                                      1, 0);
             chk(cudaGetLastError());
@@ -639,6 +656,7 @@ gbsw_status PoissonSolver::build_graph_predicted()
 
 gbsw_status PoissonSolver::enqueue()
 {
+    s_valid_ = false;  // the folds change p_hi and no stencil is stored
     if (dirty_) {
         gbsw_status st = build_graph();
         if (st != GBSW_OK) return st;
@@ -650,7 +668,21 @@ gbsw_status PoissonSolver::enqueue()
 gbsw_status PoissonSolver::enqueue_fixed(int niter, bool use_graph)
 {
     if (niter < 0) return GBSW_ERR_ARG;
-    if (!use_graph || niter > SOR_FIXED_GRAPH_MAX_ITER) return record_fixed(niter, stream);
+    if (!s_cache) {  // the stencil cache (allocated once: the captured graph holds its address)
+        const size_t n = (size_t)d.plane * (size_t)(d.nz + 2);
+        GBSW_CUDA_TRY(cudaMalloc((void **)&s_cache, n * sizeof(double)));
+        GBSW_CUDA_TRY(cudaMalloc((void **)&s_ok, sizeof(int)));
+        s_valid_ = false;
+    }
+    // the first residual may reuse the last fixed-count solve's stencil only
+    // if p_hi has not changed since
+    GBSW_CUDA_TRY(cudaMemsetAsync(s_ok, s_valid_ ? 1 : 0, sizeof(int), stream));
+    s_valid_ = false;  // set again once this solve, whose final residual stores the stencil, is enqueued
+    if (!use_graph || niter > SOR_FIXED_GRAPH_MAX_ITER) {
+        const gbsw_status st = record_fixed(niter, stream);
+        s_valid_ = st == GBSW_OK;
+        return st;
+    }
     if (!fixed_exec_ || fixed_niter_ != niter || fixed_dirty_) {
         if (fixed_exec_) cudaGraphExecDestroy(fixed_exec_);
         fixed_exec_ = nullptr;
@@ -675,6 +707,7 @@ gbsw_status PoissonSolver::enqueue_fixed(int niter, bool use_graph)
         fixed_dirty_ = false;
     }
     GBSW_CUDA_TRY(cudaGraphLaunch(fixed_exec_, stream));
+    s_valid_ = true;
     return GBSW_OK;
 }
 
@@ -685,7 +718,8 @@ gbsw_status PoissonSolver::record_fixed(int niter, cudaStream_t stream)
     const dim3 fgrid(ceil_div((d.nx + 1) / 2, 128), d.ny, d.nz), fblock(128);
     GBSW_CUDA_TRY(cudaMemsetAsync(e[0], 0, nc * sizeof(float), stream));
     GBSW_CUDA_TRY(cudaMemsetAsync(e[1], 0, nc * sizeof(float), stream));
-    poisson_resid_kernel<true><<<rgrid, POI_RED_THREADS, 0, stream>>>(d, b, p_hi, r[0], r[1], partials);
+    poisson_resid_kernel<true><<<rgrid, POI_RED_THREADS, 0, stream>>>(d, b, p_hi, r[0], r[1], partials, s_cache, s_ok,
+                                                                      nullptr);
     poisson_test_kernel<false><<<1, POI_RED_THREADS, 0, stream>>>(partials, rblocks, ctl, 0.0, niter, 0, 0, 0, 0);
     cudaError_t err = launch_iterations(d, niter, om, h2, e, r, stream);
     if (err != cudaSuccess) {
@@ -694,7 +728,8 @@ gbsw_status PoissonSolver::record_fixed(int niter, cudaStream_t stream)
     }
     poisson_fold_kernel<<<fgrid, fblock, 0, stream>>>(d, 0, p_hi, e[0]);
     poisson_fold_kernel<<<fgrid, fblock, 0, stream>>>(d, 1, p_hi, e[1]);
-    poisson_resid_kernel<false><<<rgrid, POI_RED_THREADS, 0, stream>>>(d, b, p_hi, r[0], r[1], partials);
+    poisson_resid_kernel<false><<<rgrid, POI_RED_THREADS, 0, stream>>>(d, b, p_hi, r[0], r[1], partials, nullptr,
+                                                                       nullptr, s_cache);
     poisson_test_kernel<false><<<1, POI_RED_THREADS, 0, stream>>>(partials, rblocks, ctl, 0.0, niter, niter,
                                                                    1, 0, 0);
     GBSW_LAUNCH_CHECK();

@@ -80,6 +80,9 @@ public:
     gbsw_status enqueue_fixed(int niter, bool use_graph);
     // Copy the control block of the last solve into *out (device -> device).
     gbsw_status record(PoissonCtl *dev_dst);
+    // p_hi was changed outside a solve: the next fixed-count solve forms its
+    // first residual's stencil afresh instead of reusing the stored one.
+    void invalidate_stencil_cache() { s_valid_ = false; }
 
     PDims d{};
     double *p_hi = nullptr;   // FP64 pressure (the solution)
@@ -90,6 +93,8 @@ public:
     dim3 rgrid;                   // residual grid: (ceil(nx/256), ny, ceil(nz/8)), fixed per size
     int rblocks = 0;
     PoissonCtl *ctl = nullptr;
+    double *s_cache = nullptr;    // fixed-count solves: stencil of p_hi stored by the final residual
+    int *s_ok = nullptr;          // device flag: s_cache matches p_hi
     cudaStream_t stream = nullptr;
     double omega = 1.8, tol = 1e-6;
     int max_iter = 100000, m = 10;
@@ -105,6 +110,7 @@ private:
     cudaGraphExec_t exec_ = nullptr;
     bool dirty_ = true;
     bool predict_ = false;
+    bool s_valid_ = false;  // host view of s_ok for the next fixed-count solve
 };
 
 constexpr int POI_RES_PLANES = 16;    // z-planes per thread of the residual kernel
