@@ -157,29 +157,41 @@ cudaError_t launch_stream(const gbsw_sw *s, int rows, cudaStream_t st, const flo
     return cudaGetLastError();
 }
 
-// One launch of the tile kernel of depth T (1..SWT_MAX_T).
+// One launch of the tile kernel of depth T (1..SWT_MAX_T).  after_tile: the
+// previous launch on the stream is a tile launch, so this one may start
+// programmatically (its blocks are scheduled while the previous launch
+// drains and wait in griddepcontrol.wait for its completion).
 template <int T>
 cudaError_t launch_tile(const gbsw_sw *s, cudaStream_t st, const float *eta_in, const float *u_in, const float *v_in,
-                        float *eta_out, float *u_out, float *v_out)
+                        float *eta_out, float *u_out, float *v_out, bool after_tile)
 {
-    const dim3 grid(ceil_div(s->d.nx, SWT_W), ceil_div(s->d.ny, SWT_H));
-    sw_tile_kernel<T><<<grid, SWT_THREADS, 0, st>>>(s->d, s->H, eta_in, u_in, v_in, eta_out, u_out, v_out);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ceil_div(s->d.nx, SWT_W), ceil_div(s->d.ny, SWT_H));
+    cfg.blockDim = dim3(SWT_THREADS);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = after_tile ? attr : nullptr;
+    cfg.numAttrs = after_tile ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, sw_tile_kernel<T>, s->d, (const float *)s->H, eta_in, u_in, v_in, eta_out, u_out,
+                              v_out);
 }
 
 // One launch of depth T from buffer set a into the other one, on stream st:
 // rows > 0 the streaming kernel over row segments of that height, rows < 0
-// the tile kernel.
-cudaError_t launch_from(const gbsw_sw *s, int T, int rows, int a, cudaStream_t st)
+// the tile kernel.  after_tile (tile launches only): the previous launch on
+// the stream is a tile launch.
+cudaError_t launch_from(const gbsw_sw *s, int T, int rows, int a, cudaStream_t st, bool after_tile = false)
 {
     const int b = 1 - a;
     const float *ei = s->eta[a], *ui = s->u[a], *vi = s->v[a];
     float *eo = s->eta[b], *uo = s->u[b], *vo = s->v[b];
     if (rows < 0) {
         switch (T) {
-        case 1: return launch_tile<1>(s, st, ei, ui, vi, eo, uo, vo);
-        case 2: return launch_tile<2>(s, st, ei, ui, vi, eo, uo, vo);
-        case 3: return launch_tile<3>(s, st, ei, ui, vi, eo, uo, vo);
+        case 1: return launch_tile<1>(s, st, ei, ui, vi, eo, uo, vo, after_tile);
+        case 2: return launch_tile<2>(s, st, ei, ui, vi, eo, uo, vo, after_tile);
+        case 3: return launch_tile<3>(s, st, ei, ui, vi, eo, uo, vo, after_tile);
         default: return cudaErrorInvalidValue;
         }
     }
@@ -228,7 +240,8 @@ cudaError_t chunk_graph(gbsw_sw *s, int T, int rows, int a, cudaGraphExec_t *out
     e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         cudaError_t el = cudaSuccess;
-        for (int k = 0; k < SW_CHUNK && el == cudaSuccess; ++k) el = launch_from(s, T, rows, (a + k) & 1, cs);
+        for (int k = 0; k < SW_CHUNK && el == cudaSuccess; ++k)
+            el = launch_from(s, T, rows, (a + k) & 1, cs, rows < 0 && k > 0);
         e = cudaStreamEndCapture(cs, &g);
         if (e == cudaSuccess) e = el;
     }
@@ -261,7 +274,8 @@ gbsw_status run_steps(gbsw_sw *s, int nsteps, int T, int rows)
     }
     for (int k = 0; k < full + (rest > 0); ++k) {
         const int t = k < full ? T : rest;
-        cudaError_t e = launch_from(s, t, (t == T || rows < 0) ? rows : default_rows(s, t), s->cur, s->stream);
+        cudaError_t e = launch_from(s, t, (t == T || rows < 0) ? rows : default_rows(s, t), s->cur, s->stream,
+                                    rows < 0 && k > 0);
         if (e != cudaSuccess) {
             record_cuda_error(e, "sw_stream_kernel", __FILE__, __LINE__);
             return GBSW_ERR_CUDA;

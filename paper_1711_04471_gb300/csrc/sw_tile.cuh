@@ -29,8 +29,18 @@ constexpr int SWT_W = 32, SWT_H = 32;   // written cells of a tile
 constexpr int SWT_THREADS = 1024;  // about two cells per thread and phase: the phases are short, latency-bound loops
 constexpr int SWT_MAX_T = 3;             // 6 arrays of (32 + 4T)^2 floats fit the 48 KB static limit
 
+// A load of state that the previous launch wrote: an ordered load (it may
+// not be moved above griddepcontrol.wait, as a load through the read-only
+// path may) that bypasses L1.
+__device__ __forceinline__ float ld_state(const float *ptr)
+{
+    float v;
+    asm volatile("ld.global.cg.f32 %0, [%1];" : "=f"(v) : "l"(ptr) : "memory");
+    return v;
+}
+
 template <int T>
-__global__ void __launch_bounds__(SWT_THREADS)
+__global__ void __launch_bounds__(SWT_THREADS, 2)
 sw_tile_kernel(SWDev p, const float *__restrict__ H, const float *__restrict__ eta_in, const float *__restrict__ u_in,
                const float *__restrict__ v_in, float *__restrict__ eta_out, float *__restrict__ u_out,
                float *__restrict__ v_out)
@@ -45,7 +55,7 @@ sw_tile_kernel(SWDev p, const float *__restrict__ H, const float *__restrict__ e
 
     float re[PER], ru[PER], rv[PER], rH[PER], rh[PER], rs[PER];
     int lx[PER], ly[PER];
-    bool act[PER];
+    bool act[PER], in[PER];
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
         const int q = threadIdx.x + k * SWT_THREADS;
@@ -53,19 +63,32 @@ sw_tile_kernel(SWDev p, const float *__restrict__ H, const float *__restrict__ e
         lx[k] = q % LW;
         ly[k] = q / LW;
         const int gx = x0 + lx[k], gy = y0 + ly[k];
-        float a = 0.0f, b = 0.0f, c = 0.0f, d = 0.0f;
-        if (act[k] && gx >= 0 && gx < p.nx && gy >= 0 && gy < p.ny &&
-            GBSW_INBOUNDS((long long)gy * p.pitch + gx, (long long)p.ny * p.pitch, &g_sw_bounds)) {
+        in[k] = act[k] && gx >= 0 && gx < p.nx && gy >= 0 && gy < p.ny &&
+                GBSW_INBOUNDS((long long)gy * p.pitch + gx, (long long)p.ny * p.pitch, &g_sw_bounds);
+        // H is written by no step kernel, so it may be read before the wait below
+        rH[k] = in[k] ? __ldg(H + ((size_t)gy * p.pitch + gx)) : 0.0f;
+    }
+    // Programmatic dependent launch: when this launch follows another tile
+    // launch with that dependency, its blocks may be scheduled while the
+    // previous launch drains, and they read no state before the previous
+    // launch has completed and its writes are visible.  The next launch may
+    // be scheduled as soon as every block of this one has started.  Both
+    // are no-ops for a launch without that dependency.
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int gx = x0 + lx[k], gy = y0 + ly[k];
+        float a = 0.0f, b = 0.0f, c = 0.0f;
+        if (in[k]) {
             const size_t g = (size_t)gy * p.pitch + gx;
-            a = __ldg(eta_in + g);
-            b = __ldg(u_in + g);
-            c = __ldg(v_in + g);
-            d = __ldg(H + g);
+            a = ld_state(eta_in + g);
+            b = ld_state(u_in + g);
+            c = ld_state(v_in + g);
         }
         re[k] = a;
         ru[k] = b;
         rv[k] = c;
-        rH[k] = d;
         rs[k] = 0.0f;
         // depth of the first step, and the fields the neighbours read
         rh[k] = __fadd_rn(rH[k], re[k]);

@@ -192,6 +192,30 @@ def test_tilings_and_autotune_bitwise(SW):
         assert np.array_equal(tuned[f], ref[f]), f
 
 
+@pytest.mark.parametrize("T", [1, 2, 3])
+def test_tile_launch_chains_bitwise(SW, T):
+    """Consecutive tile launches start programmatically: a launch's blocks
+    are scheduled while the previous launch still runs and wait for it
+    before they read the state.  On a grid of a few tiles many launches are
+    scheduled ahead at once, so a read that slipped ahead of the wait would
+    show here: 2,400 steps (graph chunks and direct launches) must give
+    bitwise the streaming kernel's state."""
+    inp = nudge(inputs.sw_wetdry(n=40, seed=11))
+    inp = inputs.SWInput(40, 56, inp.dx, inp.dy, inp.dt, np.vstack([inp.H, inp.H[:16]]),
+                         np.vstack([inp.eta0, inp.eta0[:16]]), hmin=inp.hmin)
+    nsteps = 2400 + T - 1
+    with SW(inp.params(), inp.H, inp.eta0) as g:
+        g.set_tiling(1, 0)
+        g.step(nsteps)
+        ref = g.get_state()
+    with SW(inp.params(), inp.H, inp.eta0) as g:
+        g.set_tiling(T, -1)
+        g.step(nsteps)
+        got = g.get_state()
+    for f in ("eta", "u", "v", "wet"):
+        assert np.array_equal(got[f], ref[f]), f
+
+
 def test_zero_steps_and_set_state_roundtrip(SW):
     inp = inputs.sw_hump(n=40)
     with SW(inp.params(), inp.H, inp.eta0) as g:
