@@ -172,8 +172,10 @@ gbsw_status sw_set_blocking(gbsw_sw *sw, int steps_per_launch);
 /* Tiling of the fused kernel: steps per launch (0 = automatic, else 1..6)
  * and the row-segment height of a thread block of the streaming kernel (0 =
  * automatic: one wave of resident blocks, segments of at least 8T rows),
- * or rows = -1 for the tile kernel (32 x 32 cells and a 2T-cell halo per
- * block in shared memory, T = 1..3), made for grids that fit in L2.
+ * or rows < 0 for the tile kernel, made for grids that fit in L2: a block
+ * holds 32 columns x h rows and a 2T-cell halo in shared memory, with
+ * h = 32 for rows = -1 and h = -rows for rows <= -2 (T = 1..3 given
+ * explicitly; h at most 52, 43, 34 for T = 1, 2, 3, else GBSW_ERR_ARG).
  * Results do not depend on the tiling (every operation is rounded as
  * written). */
 gbsw_status sw_set_tiling(gbsw_sw *sw, int steps_per_launch, int rows);
@@ -181,8 +183,10 @@ gbsw_status sw_set_tiling(gbsw_sw *sw, int steps_per_launch, int rows);
 /* Choose the tiling by measurement: times trial_steps (1..100000, rounded
  * to whole launches) on the context's own state for each depth T = 1..6
  * and row-segment heights giving the default, one, two and three waves of
- * resident blocks, and the tile kernel for T = 1..3, keeps the fastest (written to *T_out, *rows_out if
- * non-NULL) and restores the state exactly.  Allocates a copy of the state;
+ * resident blocks, and the tile kernel for T = 1..3 with 32-row tiles and
+ * with the tile height that spreads its blocks most evenly over the SMs,
+ * keeps the fastest (written to *T_out, *rows_out in the encoding of
+ * sw_set_tiling, if non-NULL) and restores the state exactly.  Allocates a copy of the state;
  * synchronous.  The paper's grids (Sec. 6.2: 500^2 to 2000^2) are small
  * enough to stay in L2, where the best tiling differs from the 4096^2
  * default. */

@@ -157,16 +157,67 @@ cudaError_t launch_stream(const gbsw_sw *s, int rows, cudaStream_t st, const flo
     return cudaGetLastError();
 }
 
-// One launch of the tile kernel of depth T (1..SWT_MAX_T).  after_tile: the
-// previous launch on the stream is a tile launch, so this one may start
-// programmatically (its blocks are scheduled while the previous launch
-// drains and wait in griddepcontrol.wait for its completion).
+// Written rows of a tile for the tiling code rows < 0: -1 the default
+// height, -h (h >= 2) h rows.
+int tile_rows(int rows) { return rows == -1 ? SWT_H : -rows; }
+
+// Resident CTAs per SM of the depth-T tile kernel.
 template <int T>
-cudaError_t launch_tile(const gbsw_sw *s, cudaStream_t st, const float *eta_in, const float *u_in, const float *v_in,
-                        float *eta_out, float *u_out, float *v_out, bool after_tile)
+int tile_per_sm()
 {
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sw_tile_kernel<T>, SWT_THREADS, 0) !=
+            cudaSuccess)
+            per_sm = 0;
+        if (per_sm < 1) per_sm = 1;
+    }
+    return per_sm;
+}
+
+int tile_per_sm(int T)
+{
+    switch (T) {
+    case 1: return tile_per_sm<1>();
+    case 2: return tile_per_sm<2>();
+    default: return tile_per_sm<3>();
+    }
+}
+
+// Tile height that spreads a tile launch most evenly over the resident
+// CTA slots: with c column tiles and S slots, h rows per tile take
+// ceil(c ceil(ny / h) / S) rounds of CTAs, each about as long as one
+// tile's (SWT_W + 4T)(h + 4T) cells of work; the least rounds x (h + 4T)
+// wins (ties: the taller tile).  Heights below 8 rows are not considered.
+int balanced_tile_rows(const gbsw_sw *s, int T)
+{
+    const long long c = ceil_div(s->d.nx, SWT_W);
+    const long long slots = (long long)tile_per_sm(T) * sm_count();
+    int best = SWT_H;
+    long long best_cost = -1;
+    for (int h = swt_max_rows(T); h >= 8; --h) {
+        const long long rounds = (c * ceil_div(s->d.ny, h) + slots - 1) / slots;
+        const long long cost = rounds * (h + 4 * T);
+        if (best_cost < 0 || cost < best_cost) {
+            best_cost = cost;
+            best = h;
+        }
+    }
+    return best;
+}
+
+// One launch of the tile kernel of depth T (1..SWT_MAX_T) with th written
+// rows per tile.  after_tile: the previous launch on the stream is a tile
+// launch, so this one may start programmatically (its blocks are scheduled
+// while the previous launch drains and wait in griddepcontrol.wait for its
+// completion).
+template <int T>
+cudaError_t launch_tile(const gbsw_sw *s, int th, cudaStream_t st, const float *eta_in, const float *u_in,
+                        const float *v_in, float *eta_out, float *u_out, float *v_out, bool after_tile)
+{
+    if (th < 2 || th > swt_max_rows(T)) return cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(ceil_div(s->d.nx, SWT_W), ceil_div(s->d.ny, SWT_H));
+    cfg.gridDim = dim3(ceil_div(s->d.nx, SWT_W), ceil_div(s->d.ny, th));
     cfg.blockDim = dim3(SWT_THREADS);
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
@@ -174,13 +225,13 @@ cudaError_t launch_tile(const gbsw_sw *s, cudaStream_t st, const float *eta_in, 
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = after_tile ? attr : nullptr;
     cfg.numAttrs = after_tile ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, sw_tile_kernel<T>, s->d, (const float *)s->H, eta_in, u_in, v_in, eta_out, u_out,
-                              v_out);
+    return cudaLaunchKernelEx(&cfg, sw_tile_kernel<T>, s->d, th, (const float *)s->H, eta_in, u_in, v_in, eta_out,
+                              u_out, v_out);
 }
 
 // One launch of depth T from buffer set a into the other one, on stream st:
 // rows > 0 the streaming kernel over row segments of that height, rows < 0
-// the tile kernel.  after_tile (tile launches only): the previous launch on
+// the tile kernel with tile_rows(rows) rows per tile.  after_tile (tile launches only): the previous launch on
 // the stream is a tile launch.
 cudaError_t launch_from(const gbsw_sw *s, int T, int rows, int a, cudaStream_t st, bool after_tile = false)
 {
@@ -189,9 +240,9 @@ cudaError_t launch_from(const gbsw_sw *s, int T, int rows, int a, cudaStream_t s
     float *eo = s->eta[b], *uo = s->u[b], *vo = s->v[b];
     if (rows < 0) {
         switch (T) {
-        case 1: return launch_tile<1>(s, st, ei, ui, vi, eo, uo, vo, after_tile);
-        case 2: return launch_tile<2>(s, st, ei, ui, vi, eo, uo, vo, after_tile);
-        case 3: return launch_tile<3>(s, st, ei, ui, vi, eo, uo, vo, after_tile);
+        case 1: return launch_tile<1>(s, tile_rows(rows), st, ei, ui, vi, eo, uo, vo, after_tile);
+        case 2: return launch_tile<2>(s, tile_rows(rows), st, ei, ui, vi, eo, uo, vo, after_tile);
+        case 3: return launch_tile<3>(s, tile_rows(rows), st, ei, ui, vi, eo, uo, vo, after_tile);
         default: return cudaErrorInvalidValue;
         }
     }
@@ -379,8 +430,10 @@ gbsw_status sw_set_blocking(gbsw_sw *s, int steps_per_launch)
 
 gbsw_status sw_set_tiling(gbsw_sw *s, int steps_per_launch, int rows)
 {
-    if (!s || steps_per_launch < 0 || steps_per_launch > SW_MAX_BLOCKING || rows < -1) return GBSW_ERR_ARG;
-    if (rows == -1 && (steps_per_launch < 1 || steps_per_launch > SWT_MAX_T)) return GBSW_ERR_ARG;
+    if (!s || steps_per_launch < 0 || steps_per_launch > SW_MAX_BLOCKING) return GBSW_ERR_ARG;
+    if (rows < 0 && (steps_per_launch < 1 || steps_per_launch > SWT_MAX_T ||
+                     tile_rows(rows) > swt_max_rows(steps_per_launch)))
+        return GBSW_ERR_ARG;
     s->blocking = steps_per_launch;
     s->rows = rows;
     return GBSW_OK;
@@ -423,10 +476,16 @@ gbsw_status sw_autotune(gbsw_sw *s, int trial_steps, int *T_out, int *rows_out)
             // segment heights: the default, and those giving 1, 2, 3 waves of resident CTAs
             const int strips = ceil_div(s->d.nx, SWS_THREADS - 4 * T);
             const int capacity = stream_per_sm(T) * sm_count();
-            int cand[5] = {default_rows(s, T), 0, 0, 0, T <= SWT_MAX_T ? -1 : 0};  // -1: the tile kernel
+            // tile kernel (T <= SWT_MAX_T): the default tile (-1) and the height
+            // that spreads its CTAs most evenly (-h)
+            int cand[6] = {default_rows(s, T), 0, 0, 0, T <= SWT_MAX_T ? -1 : 0, 0};
             for (int w = 1; w <= 3; ++w)
                 cand[w] = std::max(2, ceil_div(s->d.ny, std::max(1, ceil_div(w * capacity, strips))));
-            for (int c = 0; c < 5 && st == GBSW_OK; ++c) {
+            if (T <= SWT_MAX_T) {
+                const int h = balanced_tile_rows(s, T);
+                cand[5] = h == SWT_H ? -1 : -h;
+            }
+            for (int c = 0; c < 6 && st == GBSW_OK; ++c) {
                 if (cand[c] == 0) continue;
                 bool seen = false;
                 for (int q = 0; q < c; ++q) seen |= cand[q] == cand[c];

@@ -1,10 +1,11 @@
 // Tile kernel of the 2DSW step for grids that stay in L2 (Sec. 6.2 of
 // arXiv:1711.04471: dyn -> shapiro -> update, T steps fused per launch).
 //
-// A CTA loads a tile of SWT_W x SWT_H cells plus a halo of 2T cells on
-// every side (the dependency radius of one step is 2 cells) into shared
-// memory, advances the whole tile T steps there, and writes back the
-// middle SWT_W x SWT_H cells.  Each step is three barrier-separated
+// A CTA loads a tile of SWT_W columns x th rows (th = SWT_H unless the
+// launch picks another height, so that the CTAs spread evenly over the
+// SMs) plus a halo of 2T cells on every side (the dependency radius of one
+// step is 2 cells) into shared memory, advances the whole tile T steps
+// there, and writes back the middle SWT_W x th cells.  Each step is three barrier-separated
 // phases over the tile: momentum predictor u', v'; continuity eta*;
 // masked Shapiro filter, which also forms the next step's depth h (in the
 // other of two h buffers, since this phase still reads the current one).
@@ -25,9 +26,17 @@
 
 namespace gbsw {
 
-constexpr int SWT_W = 32, SWT_H = 32;   // written cells of a tile
-constexpr int SWT_THREADS = 1024;  // about two cells per thread and phase: the phases are short, latency-bound loops
-constexpr int SWT_MAX_T = 3;             // 6 arrays of (32 + 4T)^2 floats fit the 48 KB static limit
+constexpr int SWT_W = 32;           // written columns of a tile
+constexpr int SWT_H = 32;           // written rows of a tile unless the launch asks for another height
+constexpr int SWT_THREADS = 1024;   // about two cells per thread and phase: the phases are short, latency-bound loops
+constexpr int SWT_PER = 2;          // cells per thread
+constexpr int SWT_NC_MAX = SWT_PER * SWT_THREADS;  // cells of a tile with its halo: 6 arrays of them fill the 48 KB static limit
+constexpr int SWT_MAX_T = 3;        // a 32 x 32 tile with its halo fits up to T = 3
+
+// Most written rows of a tile of depth T: (SWT_W + 4T)(rows + 4T) <= SWT_NC_MAX
+// (52, 43 and 34 rows for T = 1, 2, 3).
+constexpr int swt_max_rows(int T) { return SWT_NC_MAX / (SWT_W + 4 * T) - 4 * T; }
+static_assert(swt_max_rows(SWT_MAX_T) >= SWT_H, "the default tile must fit at the deepest fusion");
 
 // A load of state that the previous launch wrote: an ordered load (it may
 // not be moved above griddepcontrol.wait, as a load through the read-only
@@ -39,34 +48,61 @@ __device__ __forceinline__ float ld_state(const float *ptr)
     return v;
 }
 
+// th: written rows of a tile (2 .. swt_max_rows(T), checked by the host);
+// grid = (ceil(nx / SWT_W), ceil(ny / th)).
 template <int T>
 __global__ void __launch_bounds__(SWT_THREADS, 2)
-sw_tile_kernel(SWDev p, const float *__restrict__ H, const float *__restrict__ eta_in, const float *__restrict__ u_in,
-               const float *__restrict__ v_in, float *__restrict__ eta_out, float *__restrict__ u_out,
-               float *__restrict__ v_out)
+sw_tile_kernel(SWDev p, int th, const float *__restrict__ H, const float *__restrict__ eta_in,
+               const float *__restrict__ u_in, const float *__restrict__ v_in, float *__restrict__ eta_out,
+               float *__restrict__ u_out, float *__restrict__ v_out)
 {
     constexpr int HALO = 2 * T;
-    constexpr int LW = SWT_W + 2 * HALO, LH = SWT_H + 2 * HALO, NC = LW * LH;
-    constexpr int PER = (NC + SWT_THREADS - 1) / SWT_THREADS;  // cells per thread (2 for T <= 3)
+    constexpr int LW = SWT_W + 2 * HALO;  // the row stride of the shared arrays stays a constant
+    constexpr int PER = SWT_PER;
+    const int LH = th + 2 * HALO, NC = LW * LH;  // NC <= SWT_NC_MAX
     // neighbours' values only: each thread keeps its own cells' values in registers
-    __shared__ float e[NC], uu[NC], vv[NC], hh2[2][NC], es[NC];  // depth double-buffered by step
-    const int x0 = blockIdx.x * SWT_W - HALO, y0 = blockIdx.y * SWT_H - HALO;
+    __shared__ float e[SWT_NC_MAX], uu[SWT_NC_MAX], vv[SWT_NC_MAX], hh2[2][SWT_NC_MAX],
+        es[SWT_NC_MAX];  // depth double-buffered by step
+    const int x0 = blockIdx.x * SWT_W - HALO, y0 = blockIdx.y * th - HALO;
     const float hmin = p.hmin;
 
+    // Per-cell flags, fixed for the launch: bit 3t + ph (t < T; ph = 0
+    // predictor, 1 continuity, 2 Shapiro) when the cell's row can still
+    // reach the written block in that phase (rows within 2(T - t) of it for
+    // the predictor, one fewer per later phase; the other rows hold
+    // discarded halo and are skipped), and the bits below.
+    constexpr unsigned F_EAST = 1u << 9;    // east face inside the grid and the tile
+    constexpr unsigned F_NORTH = 1u << 10;  // north face inside the grid and the tile
+    constexpr unsigned F_INNER = 1u << 11;  // not on the tile's edge: all four neighbours are in the tile
+    constexpr unsigned F_STORE = 1u << 12;  // written back (inside the written block and the grid)
+    constexpr unsigned F_LOAD = 1u << 13;   // inside the grid: loaded (else H = eta = u = v = 0)
+    constexpr unsigned F_CELL = 1u << 14;   // a cell of the tile (q < NC)
     float re[PER], ru[PER], rv[PER], rH[PER], rh[PER], rs[PER];
-    int lx[PER], ly[PER];
-    bool act[PER], in[PER];
+    unsigned m[PER];
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
         const int q = threadIdx.x + k * SWT_THREADS;
-        act[k] = q < NC;
-        lx[k] = q % LW;
-        ly[k] = q / LW;
-        const int gx = x0 + lx[k], gy = y0 + ly[k];
-        in[k] = act[k] && gx >= 0 && gx < p.nx && gy >= 0 && gy < p.ny &&
-                GBSW_INBOUNDS((long long)gy * p.pitch + gx, (long long)p.ny * p.pitch, &g_sw_bounds);
+        const int lx = q % LW, ly = q / LW;
+        const int gx = x0 + lx, gy = y0 + ly;
+        unsigned f = 0;
+        if (q < NC) {
+            f |= F_CELL;
+#pragma unroll
+            for (int t = 0; t < T; ++t)
+#pragma unroll
+                for (int ph = 0; ph < 3; ++ph)
+                    if (ly >= 2 * t + ph && ly < LH - (2 * t + ph)) f |= 1u << (3 * t + ph);
+            if (lx + 1 < LW && gx >= 0 && gx < p.nx - 1) f |= F_EAST;
+            if (ly + 1 < LH && gy >= 0 && gy < p.ny - 1) f |= F_NORTH;
+            if (lx > 0 && lx + 1 < LW && ly > 0 && ly + 1 < LH) f |= F_INNER;
+            const bool in_grid = gx >= 0 && gx < p.nx && gy >= 0 && gy < p.ny &&
+                                 GBSW_INBOUNDS((long long)gy * p.pitch + gx, (long long)p.ny * p.pitch, &g_sw_bounds);
+            if (in_grid) f |= F_LOAD;
+            if (in_grid && lx >= HALO && lx < HALO + SWT_W && ly >= HALO && ly < HALO + th) f |= F_STORE;
+        }
+        m[k] = f;
         // H is written by no step kernel, so it may be read before the wait below
-        rH[k] = in[k] ? __ldg(H + ((size_t)gy * p.pitch + gx)) : 0.0f;
+        rH[k] = (f & F_LOAD) ? __ldg(H + ((size_t)gy * p.pitch + gx)) : 0.0f;
     }
     // Programmatic dependent launch: when this launch follows another tile
     // launch with that dependency, its blocks may be scheduled while the
@@ -78,10 +114,10 @@ sw_tile_kernel(SWDev p, const float *__restrict__ H, const float *__restrict__ e
     asm volatile("griddepcontrol.wait;" ::: "memory");
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
-        const int gx = x0 + lx[k], gy = y0 + ly[k];
+        const int q = threadIdx.x + k * SWT_THREADS;
         float a = 0.0f, b = 0.0f, c = 0.0f;
-        if (in[k]) {
-            const size_t g = (size_t)gy * p.pitch + gx;
+        if (m[k] & F_LOAD) {
+            const size_t g = (size_t)(y0 + q / LW) * p.pitch + (x0 + q % LW);
             a = ld_state(eta_in + g);
             b = ld_state(u_in + g);
             c = ld_state(v_in + g);
@@ -92,9 +128,9 @@ sw_tile_kernel(SWDev p, const float *__restrict__ H, const float *__restrict__ e
         rs[k] = 0.0f;
         // depth of the first step, and the fields the neighbours read
         rh[k] = __fadd_rn(rH[k], re[k]);
-        if (act[k]) {
-            hh2[0][threadIdx.x + k * SWT_THREADS] = rh[k];
-            e[threadIdx.x + k * SWT_THREADS] = re[k];
+        if (m[k] & F_CELL) {
+            hh2[0][q] = rh[k];
+            e[q] = re[k];
         }
     }
     __syncthreads();
@@ -106,21 +142,17 @@ sw_tile_kernel(SWDev p, const float *__restrict__ H, const float *__restrict__ e
 #pragma unroll
     for (int t = 0; t < T; ++t) {
         const float *hh = hh2[t & 1];
-        // Rows that can still reach the written block: those within 2 (T - t)
-        // of it for the predictor, one fewer per later phase.  The other
-        // rows hold discarded halo, so they are skipped.
-        const int B_LO = 2 * t, C_LO = 2 * t + 1, D_LO = 2 * t + 2;  // constants once the loop is unrolled
+        const unsigned F_B = 1u << (3 * t), F_C = 1u << (3 * t + 1), F_D = 1u << (3 * t + 2);
         // momentum predictor of the east and north faces of each cell
 #pragma unroll
         for (int k = 0; k < PER; ++k) {
-            if (!act[k] || ly[k] < B_LO || ly[k] >= LH - B_LO) continue;
+            if (!(m[k] & F_B)) continue;
             const int q = threadIdx.x + k * SWT_THREADS;
-            const int gx = x0 + lx[k], gy = y0 + ly[k];
             const bool wc = rh[k] > hmin;
             float un = 0.0f, vn = 0.0f;
-            if (lx[k] + 1 < LW && gx >= 0 && gx < p.nx - 1)
+            if (m[k] & F_EAST)
                 un = sw_face_mask(sw_predict(ru[k], p.gdt_dx, e[q + 1], re[k]), wc, hh[q + 1] > hmin);
-            if (ly[k] + 1 < LH && gy >= 0 && gy < p.ny - 1)
+            if (m[k] & F_NORTH)
                 vn = sw_face_mask(sw_predict(rv[k], p.gdt_dy, e[q + LW], re[k]), wc, hh[q + LW] > hmin);
             ru[k] = un;
             rv[k] = vn;
@@ -131,10 +163,10 @@ sw_tile_kernel(SWDev p, const float *__restrict__ H, const float *__restrict__ e
         // continuity with upwind face fluxes
 #pragma unroll
         for (int k = 0; k < PER; ++k) {
-            if (!act[k] || ly[k] < C_LO || ly[k] >= LH - C_LO) continue;
+            if (!(m[k] & F_C)) continue;
             const int q = threadIdx.x + k * SWT_THREADS;
             float out = re[k];
-            if (lx[k] > 0 && lx[k] + 1 < LW && ly[k] > 0 && ly[k] + 1 < LH) {
+            if (m[k] & F_INNER) {
                 const float h1 = rh[k];
                 const float fe = sw_upwind(ru[k], h1, hh[q + 1]);
                 const float fw = sw_upwind(uu[q - 1], hh[q - 1], h1);
@@ -149,10 +181,10 @@ sw_tile_kernel(SWDev p, const float *__restrict__ H, const float *__restrict__ e
         // masked Shapiro filter on wet cells
 #pragma unroll
         for (int k = 0; k < PER; ++k) {
-            if (!act[k] || ly[k] < D_LO || ly[k] >= LH - D_LO) continue;
+            if (!(m[k] & F_D)) continue;
             const int q = threadIdx.x + k * SWT_THREADS;
             float out = rs[k];
-            if (lx[k] > 0 && lx[k] + 1 < LW && ly[k] > 0 && ly[k] + 1 < LH && rh[k] > hmin) {
+            if ((m[k] & F_INNER) && rh[k] > hmin) {
                 const float we = hh[q + 1] > hmin ? 1.0f : 0.0f;
                 const float ww = hh[q - 1] > hmin ? 1.0f : 0.0f;
                 const float wn = hh[q + LW] > hmin ? 1.0f : 0.0f;
@@ -174,15 +206,12 @@ sw_tile_kernel(SWDev p, const float *__restrict__ H, const float *__restrict__ e
     }
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
-        if (!act[k] || lx[k] < HALO || lx[k] >= HALO + SWT_W || ly[k] < HALO || ly[k] >= HALO + SWT_H) continue;
-        const int gx = x0 + lx[k], gy = y0 + ly[k];
-        if (gx < p.nx && gy < p.ny &&
-            GBSW_INBOUNDS((long long)gy * p.pitch + gx, (long long)p.ny * p.pitch, &g_sw_bounds)) {
-            const size_t g = (size_t)gy * p.pitch + gx;
-            eta_out[g] = re[k];
-            u_out[g] = ru[k];
-            v_out[g] = rv[k];
-        }
+        if (!(m[k] & F_STORE)) continue;
+        const int q = threadIdx.x + k * SWT_THREADS;
+        const size_t g = (size_t)(y0 + q / LW) * p.pitch + (x0 + q % LW);
+        eta_out[g] = re[k];
+        u_out[g] = ru[k];
+        v_out[g] = rv[k];
     }
 }
 

@@ -35,11 +35,15 @@ class SW:
         N.check(N.lib().sw_set_blocking(self._h, int(T)), "sw_set_blocking")
 
     def set_tiling(self, T: int, rows: int) -> None:
+        """Steps per launch T and the row-segment height of the streaming
+        kernel (0: automatic), or rows < 0 for the tile kernel: -1 with
+        32-row tiles, -h with h-row tiles (T = 1..3)."""
         N.check(N.lib().sw_set_tiling(self._h, int(T), int(rows)), "sw_set_tiling")
 
     def autotune(self, trial_steps: int = 60):
-        """Pick the fused depth and row-segment height by timing them on this
-        grid (the state is restored); returns (T, rows)."""
+        """Pick the fused depth and the row-segment height (or tile height,
+        rows < 0) by timing them on this grid (the state is restored);
+        returns (T, rows) in the encoding of set_tiling."""
         T, rows = C.c_int(), C.c_int()
         N.check(N.lib().sw_autotune(self._h, int(trial_steps), C.byref(T), C.byref(rows)), "sw_autotune")
         return T.value, rows.value

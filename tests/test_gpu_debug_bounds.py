@@ -33,7 +33,7 @@ from paper_1711_04471_gb300.sw import SW, SWBatch
 from paper_1711_04471_gb300.les import poisson_solve
 out = {}
 inp = inputs.sw_wetdry(n=150, seed=8)
-for T, rows in [(3, 0), (2, 5), (6, 2), (2, -1), (3, -1)]:
+for T, rows in [(3, 0), (2, 5), (6, 2), (2, -1), (3, -1), (1, -52), (3, -34), (3, -27)]:
     with SW(inp.params(), inp.H, inp.eta0) as g:
         g.set_tiling(T, rows)
         g.step(37)

@@ -171,7 +171,9 @@ def test_tilings_and_autotune_bitwise(SW):
         g.set_tiling(1, 0)
         g.step(nsteps)
         ref = g.get_state()
-    for T, rows in [(2, 3), (3, 7), (4, 150), (6, 2), (5, 40), (1, -1), (2, -1), (3, -1)]:   # -1: tile kernel
+    # rows < 0: tile kernel, -1 with 32-row tiles, -h with h-row tiles (up to 52, 43, 34 for T = 1, 2, 3)
+    for T, rows in [(2, 3), (3, 7), (4, 150), (6, 2), (5, 40), (1, -1), (2, -1), (3, -1),
+                    (1, -52), (2, -43), (3, -34), (3, -27), (2, -9), (3, -2)]:
         with SW(inp.params(), inp.H, inp.eta0) as g:
             g.set_tiling(T, rows)
             g.step(nsteps)
@@ -182,7 +184,7 @@ def test_tilings_and_autotune_bitwise(SW):
         g.step(17)
         before = g.get_state()
         T, rows = g.autotune(trial_steps=12)
-        assert 1 <= T <= 6 and (rows >= 2 or (rows == -1 and T <= 3))
+        assert 1 <= T <= 6 and (rows >= 2 or (rows < 0 and T <= 3))
         after = g.get_state()
         for f in ("eta", "u", "v", "wet"):
             assert np.array_equal(before[f], after[f]), f
@@ -192,8 +194,8 @@ def test_tilings_and_autotune_bitwise(SW):
         assert np.array_equal(tuned[f], ref[f]), f
 
 
-@pytest.mark.parametrize("T", [1, 2, 3])
-def test_tile_launch_chains_bitwise(SW, T):
+@pytest.mark.parametrize("T,rows", [(1, -1), (2, -1), (3, -1), (3, -27)])
+def test_tile_launch_chains_bitwise(SW, T, rows):
     """Consecutive tile launches start programmatically: a launch's blocks
     are scheduled while the previous launch still runs and wait for it
     before they read the state.  On a grid of a few tiles many launches are
@@ -209,7 +211,7 @@ def test_tile_launch_chains_bitwise(SW, T):
         g.step(nsteps)
         ref = g.get_state()
     with SW(inp.params(), inp.H, inp.eta0) as g:
-        g.set_tiling(T, -1)
+        g.set_tiling(T, rows)
         g.step(nsteps)
         got = g.get_state()
     for f in ("eta", "u", "v", "wet"):
@@ -241,6 +243,14 @@ def test_cfl_and_argument_errors(SW):
     assert e.value.status == -4
     with pytest.raises(GBSWError):
         SW(dict(inp.params(), nx=1, ny=1), inp.H[:1, :1], inp.eta0[:1, :1])
+    with SW(inp.params(), inp.H, inp.eta0) as g:
+        for T, rows in [(1, -52), (2, -43), (3, -34), (3, -2), (6, 1)]:
+            g.set_tiling(T, rows)
+        # the tile kernel needs T = 1..3 given explicitly and a tile whose halo fits shared memory
+        for T, rows in [(4, -1), (0, -1), (1, -53), (2, -44), (3, -35), (7, 0), (-1, 0)]:
+            with pytest.raises(GBSWError) as e:
+                g.set_tiling(T, rows)
+            assert e.value.status == -1, (T, rows)
 
 
 def test_volume_reproducible_and_conserved(SW):
