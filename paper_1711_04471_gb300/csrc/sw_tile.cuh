@@ -38,6 +38,19 @@ constexpr int SWT_MAX_T = 3;        // a 32 x 32 tile with its halo fits up to T
 constexpr int swt_max_rows(int T) { return SWT_NC_MAX / (SWT_W + 4 * T) - 4 * T; }
 static_assert(swt_max_rows(SWT_MAX_T) >= SWT_H, "the default tile must fit at the deepest fusion");
 
+// Row flags of the tile kernel of depth T as a table: the 9 bits at 9d are
+// those of a row d rows from the tile's nearer top or bottom edge (d = 0 ..
+// 2T): bit 3t + ph for every phase ph of step t with 2t + ph <= d.
+__host__ __device__ constexpr unsigned long long swt_row_bits(int T)
+{
+    unsigned long long tab = 0;
+    for (int d = 0; d <= 2 * T; ++d)
+        for (int t = 0; t < T; ++t)
+            for (int ph = 0; ph < 3; ++ph)
+                if (2 * t + ph <= d) tab |= 1ull << (9 * d + 3 * t + ph);
+    return tab;
+}
+
 // A load of state that the previous launch wrote: an ordered load (it may
 // not be moved above griddepcontrol.wait, as a load through the read-only
 // path may) that bypasses L1.
@@ -69,14 +82,16 @@ sw_tile_kernel(SWDev p, int th, const float *__restrict__ H, const float *__rest
     // Per-cell flags, fixed for the launch: bit 3t + ph (t < T; ph = 0
     // predictor, 1 continuity, 2 Shapiro) when the cell's row can still
     // reach the written block in that phase (rows within 2(T - t) of it for
-    // the predictor, one fewer per later phase; the other rows hold
-    // discarded halo and are skipped), and the bits below.
+    // the predictor, one fewer per later phase, i.e. at least 2t + ph rows
+    // from the tile's top and bottom edges; the other rows hold discarded
+    // halo and are skipped), and the bits below.
     constexpr unsigned F_EAST = 1u << 9;    // east face inside the grid and the tile
     constexpr unsigned F_NORTH = 1u << 10;  // north face inside the grid and the tile
     constexpr unsigned F_INNER = 1u << 11;  // not on the tile's edge: all four neighbours are in the tile
     constexpr unsigned F_STORE = 1u << 12;  // written back (inside the written block and the grid)
     constexpr unsigned F_LOAD = 1u << 13;   // inside the grid: loaded (else H = eta = u = v = 0)
     constexpr unsigned F_CELL = 1u << 14;   // a cell of the tile (q < NC)
+    constexpr unsigned long long ROWS = swt_row_bits(T);
     float re[PER], ru[PER], rv[PER], rH[PER], rh[PER], rs[PER];
     unsigned m[PER];
 #pragma unroll
@@ -86,15 +101,11 @@ sw_tile_kernel(SWDev p, int th, const float *__restrict__ H, const float *__rest
         const int gx = x0 + lx, gy = y0 + ly;
         unsigned f = 0;
         if (q < NC) {
-            f |= F_CELL;
-#pragma unroll
-            for (int t = 0; t < T; ++t)
-#pragma unroll
-                for (int ph = 0; ph < 3; ++ph)
-                    if (ly >= 2 * t + ph && ly < LH - (2 * t + ph)) f |= 1u << (3 * t + ph);
+            const int dy = min(ly, LH - 1 - ly);  // rows to the nearer of the tile's top and bottom edges
+            f |= F_CELL | (unsigned)((ROWS >> (9 * min(dy, 2 * T))) & 0x1ffull);
             if (lx + 1 < LW && gx >= 0 && gx < p.nx - 1) f |= F_EAST;
             if (ly + 1 < LH && gy >= 0 && gy < p.ny - 1) f |= F_NORTH;
-            if (lx > 0 && lx + 1 < LW && ly > 0 && ly + 1 < LH) f |= F_INNER;
+            if (lx > 0 && lx + 1 < LW && dy > 0) f |= F_INNER;
             const bool in_grid = gx >= 0 && gx < p.nx && gy >= 0 && gy < p.ny &&
                                  GBSW_INBOUNDS((long long)gy * p.pitch + gx, (long long)p.ny * p.pitch, &g_sw_bounds);
             if (in_grid) f |= F_LOAD;
