@@ -685,7 +685,9 @@ def run_sw_paper(args, rank, world, local):
                 oracle.use_openmp(False)
             cpu["threads"] = oracle.threads()
         res.append({"n": n, "seconds_10000_steps": t, "cell_updates_per_s": n * n * 10000 / t,
-                    "tiling": {"steps_per_launch": tiling[0], "rows_per_block": tiling[1]},
+                    "tiling": {"steps_per_launch": tiling[0], "rows_per_block": tiling[1],
+                               "kernel": ("tile, %d rows per tile" % (32 if tiling[1] == -1 else -tiling[1])
+                                          if tiling[1] < 0 else "streaming")},
                     "oracle_cell_updates_per_s_1thread": cpu.get(False),
                     "oracle_cell_updates_per_s_all_cores": cpu.get(True), "oracle_threads": cpu.get("threads")})
     if rank != 0:
