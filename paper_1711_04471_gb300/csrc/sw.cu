@@ -231,8 +231,8 @@ cudaError_t launch_tile(const gbsw_sw *s, int th, cudaStream_t st, const float *
 
 // One launch of depth T from buffer set a into the other one, on stream st:
 // rows > 0 the streaming kernel over row segments of that height, rows < 0
-// the tile kernel with tile_rows(rows) rows per tile.  after_tile (tile launches only): the previous launch on
-// the stream is a tile launch.
+// the tile kernel with tile_rows(rows) rows per tile.  after_tile (tile
+// launches only): the previous launch on the stream is a tile launch.
 cudaError_t launch_from(const gbsw_sw *s, int T, int rows, int a, cudaStream_t st, bool after_tile = false)
 {
     const int b = 1 - a;
@@ -328,7 +328,7 @@ gbsw_status run_steps(gbsw_sw *s, int nsteps, int T, int rows)
         cudaError_t e = launch_from(s, t, (t == T || rows < 0) ? rows : default_rows(s, t), s->cur, s->stream,
                                     rows < 0 && k > 0);
         if (e != cudaSuccess) {
-            record_cuda_error(e, "sw_stream_kernel", __FILE__, __LINE__);
+            record_cuda_error(e, rows < 0 ? "sw_tile_kernel" : "sw_stream_kernel", __FILE__, __LINE__);
             return GBSW_ERR_CUDA;
         }
         s->cur = 1 - s->cur;
@@ -431,8 +431,7 @@ gbsw_status sw_set_blocking(gbsw_sw *s, int steps_per_launch)
 gbsw_status sw_set_tiling(gbsw_sw *s, int steps_per_launch, int rows)
 {
     if (!s || steps_per_launch < 0 || steps_per_launch > SW_MAX_BLOCKING) return GBSW_ERR_ARG;
-    if (rows < 0 && (steps_per_launch < 1 || steps_per_launch > SWT_MAX_T ||
-                     tile_rows(rows) > swt_max_rows(steps_per_launch)))
+    if (rows < 0 && (steps_per_launch < 1 || steps_per_launch > SWT_MAX_T || rows < -swt_max_rows(steps_per_launch)))
         return GBSW_ERR_ARG;
     s->blocking = steps_per_launch;
     s->rows = rows;

@@ -247,7 +247,7 @@ def test_cfl_and_argument_errors(SW):
         for T, rows in [(1, -52), (2, -43), (3, -34), (3, -2), (6, 1)]:
             g.set_tiling(T, rows)
         # the tile kernel needs T = 1..3 given explicitly and a tile whose halo fits shared memory
-        for T, rows in [(4, -1), (0, -1), (1, -53), (2, -44), (3, -35), (7, 0), (-1, 0)]:
+        for T, rows in [(4, -1), (0, -1), (1, -53), (2, -44), (3, -35), (3, -2**31), (7, 0), (-1, 0)]:
             with pytest.raises(GBSWError) as e:
                 g.set_tiling(T, rows)
             assert e.value.status == -1, (T, rows)
