@@ -18,7 +18,11 @@
  *  - A context owns all device memory it allocates.  Entry points that take
  *    device pointers say so; the caller owns those buffers.
  *  - `stream` is a cudaStream_t passed as void*; NULL selects the legacy
- *    default stream.  Calls on one context are not thread-safe.
+ *    default stream.  Calls on one context are not thread-safe.  The library
+ *    also fills a few process-wide caches on first use (the SM count of the
+ *    device current at the first call, each kernel's resident blocks per SM,
+ *    the convolutions' shared-memory attributes): make the first call of
+ *    each kind from one host thread, on devices of one model.
  *  - Asynchronous calls (sw_step, ...) enqueue work and return; errors of
  *    the enqueued kernels surface at the next synchronising call.
  */
