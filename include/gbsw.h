@@ -71,12 +71,14 @@ const char *gbsw_last_error(void);
 gbsw_status gbsw_measure_l2_copy(long long bytes, int passes, double *gbs);
 
 /*
- * Bounds-checked debug build (SURVEY-style sanitizer substitute; the paper
- * has no counterpart).  libgbsw_debug.so, built from the same sources with
- * GBSW_DEBUG_BOUNDS=1, tests every global index of the 2DSW kernels (the
- * streaming, tile and ensemble kernels) and of the SOR sweep against its
- * buffer's extent before the access; a failed test skips the access and
- * is counted, so a wrong index never faults.  gbsw_debug_bounds writes the
+ * Bounds-checked debug build (a stand-in for a memory-checking sanitizer;
+ * the paper has no counterpart).  libgbsw_debug.so, built from the same
+ * sources with GBSW_DEBUG_BOUNDS=1, tests the global indices of the 2DSW
+ * kernels (the streaming, tile and ensemble kernels), of the SOR sweep, of
+ * the UFLES velnw, predictor and right-hand-side kernels and of the warm
+ * start's grid transfers against their buffers' extents before the
+ * access; a failed test skips the access and is counted, so a wrong index
+ * never faults.  gbsw_debug_bounds writes the
  * count since the last call to *violations (and clears it), returning
  * GBSW_ERR_DEVICE_BOUNDS if it is not 0; in the product build it writes -1
  * and returns GBSW_OK.  Synchronises the device.
